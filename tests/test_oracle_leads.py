@@ -1,0 +1,93 @@
+"""Pins of the oracle's surface Green's functions and self-energies (Eq. GR, Sec. 2.2.2)."""
+import numpy as np
+import pytest
+
+from oracle import leads as ld
+from oracle import model as mdl
+
+
+def textbook_chain(eps, t):
+    # uniform chain: g = (eps - sqrt(eps - 2|t|) sqrt(eps + 2|t|)) / (2 t^2); the product of
+    # two principal roots is the branch that is analytic in the upper half plane
+    a = abs(t)
+    return (eps - np.sqrt(eps - 2 * a) * np.sqrt(eps + 2 * a)) / (2 * a * a)
+
+
+def test_uniform_chain_reduces_to_textbook():
+    t = -2.7
+    E = np.linspace(-7, 7, 301)
+    for eps in (E + 1e-6j, E + 0.3j, -3 + 2.0 * np.exp(1j * np.linspace(0.01, 3.1, 50))):
+        g = ld.surface_gf_dimer(eps, t * t, t * t)
+        assert np.max(np.abs(g - textbook_chain(eps, t))) < 1e-10
+
+
+@pytest.mark.parametrize("a1,a2", [(2.7 ** 2, (2 * 2.7 * np.cos(np.pi / 17)) ** 2),
+                                   (2.7 ** 2, (2 * 2.7 * np.cos(6 * np.pi / 17)) ** 2),
+                                   ((2 * 2.7 * np.cos(6 * np.pi / 17)) ** 2, 2.7 ** 2),
+                                   (1.0, 0.0), (0.0, 4.0)])
+def test_dimer_root_is_retarded_and_solves_recursion(a1, a2):
+    E = np.linspace(-9, 9, 2001)
+    for eps in (E + 1e-6j, E + 1e-3j):
+        g = ld.surface_gf_dimer(eps, a1, a2)
+        assert np.all(g.imag <= 0.0)
+        # the defining recursion g = 1/(eps - a1/(eps - a2 g))
+        rhs = 1.0 / (eps - a1 / (eps - a2 * g))
+        assert np.max(np.abs(g - rhs) / np.abs(g)) < 1e-9
+    z = -4 + 5 * np.exp(1j * np.linspace(0.001, np.pi - 0.001, 300))
+    g = ld.surface_gf_dimer(z, a1, a2)
+    assert np.all(g.imag < 0)
+
+
+def _away_from_edges(E, edges, margin):
+    return np.array([e for e in E if np.min(np.abs(e - np.asarray(edges))) > margin])
+
+
+def test_analytic_matches_decimation_mode_chain():
+    n, t = 17, -2.7
+    for j in (1, 6):
+        ch = mdl.mode_chain(n, j, t, 8, 0.05, -0.1)
+        bj = abs(mdl.mode_hopping(n, j, t))
+        edges = [s * e for s in (1, -1) for e in (abs(abs(t) - bj), abs(t) + bj)]
+        for lead in (ch.lead_S, ch.lead_D):
+            # band edges and the zero-energy surface state of zigzag-terminated leads
+            E = _away_from_edges(np.linspace(-6, 6, 241), np.array(edges + [0.0]) + lead.U, 0.02)
+            for eps in (E + 1e-6j, -3 + 4 * np.exp(1j * np.linspace(0.05, 3.0, 20))):
+                sa = ld.lead_sigma_analytic(lead, eps)
+                ss = ld.lead_sigma_sancho(lead, eps)
+                assert np.max(np.abs(sa - ss)) < 1e-9 * max(1.0, np.max(np.abs(ss)))
+
+
+def test_analytic_matches_decimation_realspace_lead():
+    n, t = 7, -2.7
+    ch = mdl.realspace_chain(n, t, 8, 0.0, -0.2)
+    c = np.abs(np.cos(np.pi * np.arange(n) / n))
+    edges = np.concatenate([np.abs(1 - 2 * c), 1 + 2 * c]) * abs(t)
+    edges = np.concatenate([edges, -edges])
+    for lead in (ch.lead_S, ch.lead_D):
+        E = _away_from_edges(np.linspace(-8, 8, 97), np.append(edges, 0.0) + lead.U, 0.02)
+        eps = E + 1e-6j
+        sa = ld.lead_sigma_analytic(lead, eps)
+        ss = ld.lead_sigma_sancho(lead, eps)
+        assert np.max(np.abs(sa - ss)) < 1e-9 * max(1.0, np.max(np.abs(ss)))
+        gam = ld.broadening(sa)
+        ev = np.linalg.eigvalsh(0.5 * (gam + np.conj(np.swapaxes(gam, 1, 2))))
+        assert ev.min() > -1e-12
+
+
+def test_non_circulant_lead_rejected_by_analytic():
+    lead = mdl.Lead(0.0, np.diag([1.0, 2.0]).astype(complex), np.eye(2, dtype=complex),
+                    np.eye(2, dtype=complex), np.arange(2))
+    with pytest.raises(ValueError):
+        ld.lead_sigma_analytic(lead, np.array([0.1 + 1e-6j]))
+
+
+def test_zigzag_surface_state_pole():
+    # a lead whose surface bond is the weaker one (|t| < |b_j|) has a bound surface state at
+    # eps = 0: g ~ (1 - a1/a2)/eps, so Sigma grows like 1/eta at E = U_lead
+    t, b = 2.7, 2 * 2.7 * np.cos(np.pi / 17)
+    for eta in (1e-3, 1e-6):
+        g = ld.surface_gf_dimer(np.array([1j * eta]), t * t, b * b)[0]
+        assert abs(g * 1j * eta - (1 - t * t / (b * b))) < 10 * eta
+    # the other termination has no surface state: g -> 0 like eps/(a2 - a1)
+    g = ld.surface_gf_dimer(np.array([1e-6j]), b * b, t * t)[0]
+    assert abs(g) < 1e-5

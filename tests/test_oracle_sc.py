@@ -1,0 +1,91 @@
+"""Pins of the oracle's Broyden mixing (Alg. 3), 1D Poisson stand-in and SC loop."""
+import numpy as np
+import pytest
+
+from oracle import selfconsistent as sc
+from oracle import charge as chg
+from oracle import model as mdl
+from oracle import quadrature as q
+
+
+def test_thomas_matches_dense_solve():
+    rng = np.random.default_rng(0)
+    n = 50
+    sub = rng.uniform(-1, 0, n)
+    sup = rng.uniform(-1, 0, n)
+    dia = 3 + rng.uniform(0, 1, n)
+    rhs = rng.normal(size=n)
+    A = np.diag(dia) + np.diag(sub[1:], -1) + np.diag(sup[:-1], 1)
+    assert np.max(np.abs(sc.thomas(sub, dia, sup, rhs) - np.linalg.solve(A, rhs))) < 1e-13
+
+
+def test_poisson_closed_form_without_charge():
+    # n == n0: U_i - U_G = A mu^(i+1) + B mu^-(i+1), mu + 1/mu = (1 + 2r)/r
+    p = sc.PoissonParams(kappa=19.4, lam_nm=3.0, U_G=-0.2, U_S=0.0, U_D=-0.4)
+    N = 200
+    U = sc.poisson_solve(np.ones(N), np.ones(N), p)
+    r = p.r
+    s = (1 + 2 * r) / r
+    mu = (s - np.sqrt(s * s - 4)) / 2
+    # boundary nodes i = -1 -> k = 0 and i = N -> k = N + 1
+    k = np.arange(1, N + 1)
+    a0, aN = p.U_S - p.U_G, p.U_D - p.U_G
+    M = np.array([[1.0, 1.0], [mu ** (N + 1), mu ** -(N + 1)]])
+    A, B = np.linalg.solve(M, [a0, aN])
+    closed = p.U_G + A * mu ** k + B * mu ** (-k.astype(float))
+    assert np.max(np.abs(U - closed)) < 1e-10
+
+
+def test_poisson_charge_inverts_solve():
+    p = sc.PoissonParams(kappa=sc.kappa_from_geometry(), U_G=-0.2, U_S=0.0, U_D=-0.4)
+    rng = np.random.default_rng(1)
+    n0 = np.full(64, 4.0)
+    n = n0 + rng.normal(scale=0.01, size=64)
+    U = sc.poisson_solve(n, n0, p)
+    assert np.max(np.abs(sc.poisson_charge(U, n0, p) - n)) < 1e-11
+    assert 18.0 < p.kappa < 21.0
+
+
+def nonlinear_map(x):
+    A = np.array([[0.5, 0.1, 0.0], [0.1, 0.4, 0.2], [0.0, 0.2, 0.3]])
+    return 2.0 + 0.3 * np.tanh(A @ x) + 0.05 * x
+
+
+def test_broyden_vw_equals_dense_rank_one_form():
+    x0 = np.array([1.0, 2.0, 3.0])
+    a = sc.Broyden(x0, 0.3, 16)
+    b = sc.BroydenDense(x0, 0.3)
+    for _ in range(10):
+        ya = a.step(nonlinear_map(a.n_in))
+        yb = b.step(nonlinear_map(b.n_in))
+        assert np.max(np.abs(ya - yb)) < 1e-12 * np.max(np.abs(yb))
+
+
+def test_broyden_converges_on_linear_map():
+    rng = np.random.default_rng(2)
+    N = 20
+    A = rng.normal(scale=0.3, size=(N, N)) / np.sqrt(N)
+    c = rng.uniform(1, 2, N)
+    fixed = np.linalg.solve(np.eye(N) - A, c)
+    br = sc.Broyden(np.ones(N), 0.5, 64)
+    for it in range(60):
+        out = A @ br.n_in + c
+        if sc.residual(br.n_in, out) < 1e-13:
+            break
+        br.step(out)
+    assert np.max(np.abs(br.n_in - fixed)) < 1e-11 * np.max(np.abs(fixed))
+
+
+def test_sc_loop_reaches_fixed_point():
+    N = 16
+    dev = mdl.cnt_build("mode", 17, -2.7, N, 0.0, -0.1, modes=(6,))
+    grid = q.bias_grid(0.0, -0.1, 0.025, 48, 16, E_B=-10.0, eta=1e-6)
+    n0 = chg.neutral_charge(dev, 16, -10.0)
+    p = sc.PoissonParams(kappa=sc.kappa_from_geometry(), U_G=-0.2, U_S=0.0, U_D=-0.1)
+    U0 = np.linspace(0, -0.1, N)
+    ev = lambda U: chg.negf_evaluate(dev, U, grid)
+    res = sc.sc_solve(ev, U0, n0, p, zeta=0.1, M=64, tol=1e-9)
+    assert res["converged"]
+    U = sc.poisson_solve(res["n_in"], n0, p)
+    n_out = ev(U)["n"]
+    assert sc.residual(res["n_in"], n_out) < 1e-9
