@@ -29,7 +29,7 @@ Parity: pinned (dense == recursion, sum rule i(G - G^dagger) = G (Gamma_S + Gamm
 plateaus, real space == sum of mode chains).
 """
 import numpy as np
-from .leads import lead_sigma, broadening
+from .leads import lead_sigma, broadening, lead_sigma_gamma_analytic
 
 
 def _embed(blocks, sites, b):
@@ -40,7 +40,14 @@ def _embed(blocks, sites, b):
 
 
 def contact_blocks(chain, eps, method="analytic"):
-    """Sigma_S on layer 0 and Sigma_D on layer L-1, as (E, b, b) stacks, and their Gammas."""
+    """Sigma_S on layer 0 and Sigma_D on layer L-1, as (E, b, b) stacks, and their Gammas
+    (Gamma = i (Sigma - Sigma^dagger); analytic leads evaluate it in the mode basis)."""
+    if method == "analytic":
+        out = []
+        for lead in (chain.lead_S, chain.lead_D):
+            s, gm = lead_sigma_gamma_analytic(lead, eps)
+            out.append((_embed(s, lead.sites, chain.b), _embed(gm, lead.sites, chain.b)))
+        return out[0][0], out[1][0], out[0][1], out[1][1]
     sS = _embed(lead_sigma(chain.lead_S, eps, method), chain.lead_S.sites, chain.b)
     sD = _embed(lead_sigma(chain.lead_D, eps, method), chain.lead_D.sites, chain.b)
     return sS, sD, broadening(sS), broadening(sD)

@@ -82,6 +82,16 @@ def fourier_matrix(m):
 
 def lead_sigma_analytic(lead, eps):
     """Sigma (E, m, m) of a lead with circulant couplings, closed form per angular mode."""
+    return lead_sigma_gamma_analytic(lead, eps)[0]
+
+
+def lead_sigma_gamma_analytic(lead, eps):
+    """Sigma and Gamma (E, m, m) of a circulant lead.
+
+    Gamma = i (Sigma - Sigma^dagger) is evaluated in the ring Fourier basis, where Sigma is
+    diagonal: Gamma = F diag(i (sigma_j - conj sigma_j)) F^dagger = F diag(-2 Im sigma_j) F^dagger.
+    This is the same matrix as the site-basis difference, without its cancellation when
+    every mode is closed (Gamma ~ eta, far below |Sigma|)."""
     eps = np.atleast_1d(np.asarray(eps, complex))
     a1 = np.abs(circulant_eigenvalues(lead.T1)) ** 2
     a2 = np.abs(circulant_eigenvalues(lead.T2)) ** 2
@@ -92,7 +102,9 @@ def lead_sigma_analytic(lead, eps):
                          np.broadcast_to(a2, (eps.size, a1.size)))
     sig = at[None, :] * g                       # (E, m) per-mode self-energies
     F = fourier_matrix(lead.m)
-    return np.einsum("sj,ej,tj->est", F, sig, F.conj())
+    Sigma = np.einsum("sj,ej,tj->est", F, sig, F.conj())
+    Gamma = np.einsum("sj,ej,tj->est", F, (-2.0 * sig.imag).astype(complex), F.conj())
+    return Sigma, Gamma
 
 
 def surface_gf_sancho(eps, H00, H01, tol=1e-14, max_iter=400):

@@ -91,3 +91,23 @@ def test_zigzag_surface_state_pole():
     # the other termination has no surface state: g -> 0 like eps/(a2 - a1)
     g = ld.surface_gf_dimer(np.array([1e-6j]), b * b, t * t)[0]
     assert abs(g) < 1e-5
+
+
+def test_mode_basis_gamma_is_the_definition():
+    # Gamma = i (Sigma - Sigma^dagger); for a circulant lead both evaluations agree to
+    # rounding of |Sigma|, and the mode-basis one keeps relative accuracy when Gamma ~ eta
+    ch = mdl.realspace_chain(5, -2.7, 6, 0.0, -0.4)
+    eps = np.array([-0.3 + 1e-6j, 0.1 + 1e-6j, -3.0 + 1e-6j, -2 + 0.5j])
+    for lead in (ch.lead_S, ch.lead_D):
+        s, gm = ld.lead_sigma_gamma_analytic(lead, eps)
+        assert np.max(np.abs(gm - ld.broadening(s))) < 1e-14 * max(1.0, np.abs(s).max())
+        ev = np.linalg.eigvalsh(gm)
+        assert ev.min() >= -1e-300
+    # its eigenvalues are -2 Im sigma_j of the per-mode closed form
+    lead = ch.lead_S
+    s, gm = ld.lead_sigma_gamma_analytic(lead, np.array([0.1 + 1e-6j]))
+    a1 = np.abs(ld.circulant_eigenvalues(lead.T1)) ** 2
+    a2 = np.abs(ld.circulant_eigenvalues(lead.T2)) ** 2
+    at = np.abs(ld.circulant_eigenvalues(lead.tau)) ** 2
+    sig = at * ld.surface_gf_dimer(np.full(5, 0.1 + 1e-6j - lead.U), a1, a2)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(gm[0])), np.sort(-2 * sig.imag), rtol=1e-12, atol=1e-18)
