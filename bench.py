@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark of the energy-parallel NEGF hot path on GB300.
+
+Workload: (17,0) nanotube in real space, 17 x 17 complex128 ring blocks, N = 512 rings,
+2048 Gauss-Legendre real-axis energies + 128 contour nodes, V_DS = 0.4 V, V_GS = 0.2 V
+(seeded synthetic potential: sum of 8 sinusoids, 0.15 eV), self-consistent with Broyden
+mixing and the 1D Poisson stand-in.
+
+One step = one self-consistent iteration of the whole hot path: Poisson -> contact
+self-energies -> forward/backward recursive Green's function sweeps of every energy ->
+Fermi-weighted quadrature to ring charge, T(E) and current -> Broyden update, replayed as
+one captured CUDA graph.  Metric: RGF ring-energy updates per second (rings x energies per
+step / step time).  Under torchrun each rank solves its own bias point (V_GS shifted per
+rank), no collective on the data path: weak scaling.
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a bounded sample of the
+same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "cnt17_realspace_N512_E2048+128_sc"
+
+
+def algorithmic_flops(b, m, nnz, L, n_real, n_cont):
+    """FLOPs of one NEGF evaluation in the method's formulation (8 per complex MAC):
+    real-axis lane per layer: block inverse b^3 + lead-column products R, K, G R (3 b^2 m)
+    + two dense products of the G_ll update (2 b^3) + four coupling products (4 b^2 nnz);
+    contour lane per layer: inverse + G_ll update (3 b^3) + four coupling products."""
+    real = 3 * b ** 3 + 3 * b * b * m + 4 * b * b * nnz
+    cont = 3 * b ** 3 + 4 * b * b * nnz
+    return 8.0 * L * (n_real * real + n_cont * cont)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def build_workload(ctx, negf, synth, V_GS):
+    w = synth.realspace_17()
+    dev = ctx.device_create(w["N"], block=17, rings_per_block=1, n_chains=1)
+    ctx.build_cnt_realspace(dev, 17, w["t"], w["U_S"], w["U_D"])
+    ctx.set_potential(dev, w["U"])
+    ctx.set_grid_spec(dev, w["mu_S"], w["mu_D"], w["kT"], w["eta"], w["E_B"], w["n_real"], w["n_cont"])
+    return dev, w
+
+
+def cpu_sample(n_real=256, n_cont=16, chunk=16):
+    """The oracle as it stands on a bounded sample of the workload: the first n_real
+    real-axis energies and n_cont contour nodes of the full N = 512 device.  Runs in a
+    single-threaded subprocess; returns (seconds, ring-energy updates)."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+from paper_2407_14633_gb300 import synth
+from oracle import model, green, quadrature as q
+w = synth.realspace_17()
+ch = model.realspace_chain(17, w["t"], w["N"], w["U_S"], w["U_D"])
+g = q.bias_grid(w["mu_S"], w["mu_D"], w["kT"], w["n_real"], w["n_cont"], w["E_B"], w["eta"])
+t = time.perf_counter()
+for k0 in range(0, %d, %d):
+    green.rgf_lanes(ch, w["U"], g["E"][k0:k0 + %d] + 1j * g["eta"])
+for k0 in range(0, %d, %d):
+    green.rgf_lanes(ch, w["U"], g["z"][k0:k0 + %d], spectral=False)
+print(json.dumps(dict(seconds=time.perf_counter() - t, updates=w["N"] * (%d + %d))))
+""" % (ROOT, n_real, chunk, chunk, n_cont, chunk, chunk, n_real, n_cont)
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return r["seconds"], r["updates"]
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    per_step = (32, 4)
+    for _ in range(args.warmup):
+        cpu_sample(*per_step)
+    secs, upd = 0.0, 0
+    for _ in range(args.steps):
+        s, u = cpu_sample(*per_step)
+        secs += s
+        upd += u
+    value = upd / secs
+    line = {
+        "impl": "reference", "metric": "RGF ring-energy updates/s", "value": value,
+        "unit": "ring-energy updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_per_step": "32 real-axis + 4 contour energies at full N=512"},
+        "cpu_baseline": {"value": value, "unit": "ring-energy updates/s", "cores": 1, "kind": "oracle",
+                         "sample": "32 real-axis + 4 contour energies of the N=512 workload per step"},
+        "e2e": {"value": value, "unit": "ring-energy updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2407_14633_gb300 import negf, synth
+    # a real (non-default) stream: the library launches on it and the events below are
+    # recorded on it, so they bracket exactly the library's work
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = negf.Context(device=local, stream=stream.cuda_stream)
+    V_GS = 0.2 + 0.05 * rank
+    dev, w = build_workload(ctx, negf, synth, V_GS)
+    N, n_real, n_cont = w["N"], w["n_real"], w["n_cont"]
+    units_per_step = N * (n_real + n_cont)
+    kappa = negf.poisson_kappa()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed: K self-consistent iterations (graph replays); L2 flushed between steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    M = min(256, args.warmup + args.steps + 2)
+    ctx.sc_begin(dev, w["V_DS"], V_GS, w["U"], kappa, M=M, tol=1e-300)
+    ctx.sc_step(dev, args.warmup, wait=True)
+    barrier()
+    clk = Clocks(local)
+    clk.start()
+    l0 = ctx.launch_count()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.sc_step(dev, 1, wait=False)
+        e1.record(stream)
+        evs.append((e0, e1))
+    barrier()
+    launches = ctx.launch_count() - l0
+    clocks = clk.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ctx.sc_end(dev)
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * units_per_step / (t_max * 1e-3)
+
+    # ---- dominant kernel: the block sweep, timed with events on the launching stream
+    ctx.profile(True)
+    n_t = torch.empty(N, dtype=torch.float64, device="cuda")
+    T_t = torch.empty(n_real, dtype=torch.float64, device="cuda")
+    I_t = torch.empty(1, dtype=torch.float64, device="cuda")
+    outs = [dict(n=n_t.data_ptr(), T=T_t.data_ptr(), I=I_t.data_ptr())]
+    ctx.kernel_time()
+    reps = 3
+    for _ in range(reps):
+        ctx.compute_device([dev], outs)
+    torch.cuda.synchronize()
+    sweep_ms, sweeps = ctx.kernel_time()
+    ctx.profile(False)
+    sweep_ms /= max(sweeps, 1)
+    flops = algorithmic_flops(17, 17, 1.5, N, n_real, n_cont)
+    achieved = flops / (sweep_ms * 1e-3) / 1e12
+    props = torch.cuda.get_device_properties(local)
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak_derived = 2.0 * 2.0 * props.multi_processor_count * sm_max * 1e6 / 1e12   # 2 FP64 FMA/clk/SM
+    peak_probe = ctx.fp64_peak()
+
+    # ---- end to end through the public API with host buffers
+    U_host = np.ascontiguousarray(w["U"])
+    e2e_reps = max(2, min(args.steps, 5))
+    ctx.set_potential(dev, U_host)
+    ctx.compute([dev])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_reps):
+        ctx.set_potential(dev, U_host)
+        r = ctx.compute([dev])[0]
+    t_e2e = (time.perf_counter() - t0) / e2e_reps
+    h2d = U_host.nbytes
+    d2h = 8 * (3 * N + n_real + 1)
+
+    # ---- full bias-point solve to tolerance (the second metric)
+    sc = None
+    if not args.no_solve:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = ctx.sc_solve(dev, w["V_DS"], V_GS, w["U"], kappa, zeta=w["zeta"], M=w["M"], tol=w["tol"], check=False)
+        t_solve = time.perf_counter() - t0
+        sc = {"bias_point_solves_per_s": 1.0 / t_solve, "seconds": t_solve, "iterations": res["iterations"],
+              "converged": res["converged"], "final_residual": float(res["history"][-1]) if res["iterations"] else None,
+              "current_A": res["I"]}
+
+    line = {
+        "metric": "RGF ring-energy updates/s", "value": value, "unit": "ring-energy updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_rings": N, "block": 17, "energies_real": n_real,
+                   "energies_contour": n_cont, "step": "one self-consistent iteration (captured graph)",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas per rank (weak)"},
+        "e2e": {"value": units_per_step / t_e2e, "unit": "ring-energy updates/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "call": "negf_set_potential + negf_compute, host buffers"},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "sweep_blk_kernel", "bound": "alu", "achieved": achieved,
+                     "peak": peak_derived, "unit": "TFLOP/s", "frac": achieved / peak_derived,
+                     "peak_kind": "FP64 derived: 2 FMA/clk/SM x SMs x max SM clock",
+                     "peak_probe": peak_probe, "frac_of_probe": achieved / peak_probe,
+                     "traffic": None, "kernel_ms": sweep_ms, "flops_per_launch": flops},
+        "clocks": clocks,
+        "self_consistent_solve": sc,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        secs, upd = cpu_sample()
+        line["cpu_baseline"] = {"value": upd / secs, "unit": "ring-energy updates/s", "cores": 1,
+                                "kind": "oracle", "sample": "256 real-axis + 16 contour energies of the N=512 workload"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

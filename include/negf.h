@@ -1,0 +1,305 @@
+/*
+ * negf.h -- C ABI of the GB300-native energy-parallel NEGF / recursive Green's function
+ * library (libnegf.so), after ELEQTRONeX, arXiv 2407.14633.
+ *
+ * What it computes.  For a block-tridiagonal tight-binding channel (Sec. 2.2.1: the
+ * Hamiltonian is block tridiagonal with the electrostatic potential energy on its
+ * diagonal) attached to two semi-infinite leads, and for every energy of an equilibrium
+ * complex contour and of the real-axis bias window (Eq. Rho), the library forms the
+ * contact self-energies (Eq. GR), the diagonal blocks of G^R and of the lead spectral
+ * functions A_l = G Gamma_l G^dagger (Alg. 1 / Alg. 2), the transmission
+ * T(E) = Tr[Gamma_S G Gamma_D G^dagger] (Eq. deviceCharacteristics) and reduces them by
+ * Fermi-weighted quadrature to per-ring electron counts and the current.  A Broyden
+ * mixed self-consistent loop (Alg. 3) with a 1D Poisson stand-in closes the loop with
+ * electrostatics.  Everything after the host set-up calls runs in CUDA kernels on one
+ * GPU (sm_103a).
+ *
+ * Conventions (all calls):
+ *   - Every call returns an int status: NEGF_OK (0) or a negative NEGF_E* code.  On error
+ *     nothing the caller owns is modified except where stated, and the context's last
+ *     error message (negf_last_error) describes the failure.
+ *   - Complex numbers are interleaved pairs double[2] = {re, im} (C99 double _Complex
+ *     layout).  Matrices are row-major; a stack of blocks is contiguous block after block.
+ *   - Host arrays passed in are copied before the call returns; the caller keeps
+ *     ownership and may free or reuse them.  No call keeps a caller pointer.
+ *   - Output arrays are caller-owned host memory unless a call says "device".
+ *   - Units: energies and potential energies in eV, voltages in V, lengths in nm,
+ *     kT in eV, current in A.  Electron counts are dimensionless (the paper's rho is
+ *     minus the electron density, Eq. Rho; this API reports electron counts n).
+ *   - One context per host thread, or external locking.
+ */
+#ifndef NEGF_H
+#define NEGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------------- */
+#define NEGF_OK 0
+#define NEGF_EINVAL (-1)        /* bad argument, size or state                       */
+#define NEGF_ENOMEM (-2)        /* device or host allocation failed / over budget    */
+#define NEGF_ECUDA (-3)         /* a CUDA runtime call failed                        */
+#define NEGF_ETIMEDOUT (-4)     /* a bounded wait ran out                            */
+#define NEGF_ENOTCONVERGED (-5) /* the self-consistent loop hit its iteration limit  */
+#define NEGF_EBUSY (-6)         /* the request is still running                      */
+#define NEGF_ENOTFOUND (-7)     /* unknown handle or ticket                          */
+
+/* ---- precision policy ------------------------------------------------------------ */
+#define NEGF_PREC_FP64 0   /* complex128 sweep, FP64 everywhere                          */
+#define NEGF_PREC_MIXED 1  /* complex64 sweep; flagged energies recomputed in FP64       */
+#define NEGF_PREC_FP32 2   /* complex64 sweep only (FP64 lead roots and accumulation)    */
+
+/* ---- lead sides --------------------------------------------------------------------- */
+#define NEGF_SOURCE 0
+#define NEGF_DRAIN 1
+
+/* ---- grid rules ------------------------------------------------------------------------ */
+#define NEGF_RULE_GAUSS 0      /* Gauss-Legendre on [E_min, E_max]                    */
+#define NEGF_RULE_MIDPOINT 1   /* midpoint rule on [E_min, E_max]                     */
+
+typedef struct negf_ctx negf_ctx;
+
+/* Context options.  stream: a cudaStream_t to run on (e.g. torch.cuda.Stream.cuda_stream),
+ * or NULL for a library-owned stream.  hbm_budget_bytes: cap on the library's device
+ * memory (0 = no cap); allocations beyond it fail with NEGF_ENOMEM.  precision: one of
+ * NEGF_PREC_*.  flag_threshold: mixed precision, the per-energy sum-rule residual above
+ * which an energy is recomputed in FP64.  edge_window: mixed precision, energies closer
+ * than this (eV) to a lead subband edge are recomputed in FP64.  fault_alloc_after:
+ * host-side fault injection for tests, the n-th arena allocation fails (0 = off). */
+typedef struct {
+  int device_ordinal;
+  void* stream;
+  size_t hbm_budget_bytes;
+  int precision;
+  double flag_threshold;
+  double edge_window;
+  int fault_alloc_after;
+} negf_opts;
+
+/* Create / destroy a context on one GPU.  opts may be NULL (defaults: device 0, own
+ * stream, no budget, FP64).  negf_destroy frees every device buffer the context owns. */
+int negf_create(negf_ctx** out, const negf_opts* opts);
+int negf_destroy(negf_ctx* ctx);
+
+/* Static description of a status code, and the context's last error message. */
+const char* negf_strerror(int status);
+const char* negf_last_error(const negf_ctx* ctx);
+
+/* ---- devices (Sec. 2.2.1 block-tridiagonal H, Sec. 2.2.2 multi-mode arrays) -------- */
+
+/* A device is a channel of n_rings rings made of n_chains independent block-tridiagonal
+ * chains sharing one potential (several mode-space subbands are independent chains,
+ * Sec. 2.2.2).  Each chain has L = n_rings / rings_per_block layers of width `block`;
+ * site a of layer l belongs to ring l * rings_per_block + a / (block / rings_per_block).
+ * Supported: block in 1..64, rings_per_block in {1, 2} dividing block and n_rings.
+ * Returns the device handle in *dev. */
+int negf_device_create(negf_ctx* ctx, int n_rings, int block, int rings_per_block,
+                       int n_chains, int* dev);
+int negf_device_destroy(negf_ctx* ctx, int dev);
+
+/* Hamiltonian of one chain without the electrostatic potential (Sec. 2.2.1):
+ * Hdiag: L blocks H_{l,l} (L*block*block complex), Hup: L-1 blocks H_{l,l+1}
+ * ((L-1)*block*block complex); the lower blocks are Hup^dagger (H Hermitian).
+ * g_b: band degeneracy of the chain (the spin degeneracy g_s = 2 is fixed). */
+int negf_set_hamiltonian(negf_ctx* ctx, int dev, int chain, const double* Hdiag,
+                         const double* Hup, double g_b);
+
+/* Semi-infinite lead of one chain (Eq. GR, Sec. 2.2.2).  The lead is a sequence of rings
+ * s0, s1, ... moving away from the device with m sites each, on-site potential energy
+ * U_lead, couplings H_{s1,s0} = T1, H_{s2,s1} = T2, H_{s3,s2} = T1, ... and device
+ * coupling tau = H_{s0, boundary ring}.  T1, T2, tau must be circulant m x m matrices and
+ * are given by their first rows (m complex each); their surface Green's function is then
+ * the closed-form root of each angular mode (the analytic nanotube lead the paper uses).
+ * sites: the m site indices (0..block-1) of the boundary ring inside the first (source)
+ * or last (drain) layer.  side: NEGF_SOURCE or NEGF_DRAIN. */
+typedef struct {
+  int m;
+  double U_lead;
+  const double* T1;
+  const double* T2;
+  const double* tau;
+  const int* sites;
+} negf_lead;
+int negf_set_lead(negf_ctx* ctx, int dev, int chain, int side, const negf_lead* lead);
+
+/* Lead potential energies only (U_S, U_D), keeping the couplings. */
+int negf_set_lead_potentials(negf_ctx* ctx, int dev, double U_S, double U_D);
+
+/* Convenience builders for (n,0) zigzag nanotubes with nearest-neighbour coupling t
+ * (Sec. 3.1), leads continuing the tube, lead potentials U_S / U_D.
+ * Mode space: chain c is subband modes[c] (bond k = t for even k, 2 t cos(pi j / n) for
+ * odd k, g_b = 2); a device created with block = 2, rings_per_block = 2 groups rings
+ * (2l, 2l+1) into 2 x 2 unit-cell blocks.  Real space: n x n ring blocks,
+ * bonds t I and t (I + S) / t (I + S^T) alternating, g_b = 1 (block = n, one chain). */
+int negf_build_cnt_modespace(negf_ctx* ctx, int dev, int n_tube, double t, const int* modes,
+                             double U_S, double U_D);
+int negf_build_cnt_realspace(negf_ctx* ctx, int dev, int n_tube, double t, double U_S,
+                             double U_D);
+
+/* Electrostatic potential energy per ring (n_rings doubles), added to every site of the
+ * ring (Sec. 2.2.1: the diagonal of H is -e phi per ring). */
+int negf_set_potential(negf_ctx* ctx, int dev, const double* U);
+
+/* ---- energy grids (Eq. Rho) ----------------------------------------------------------- */
+
+/* An energy grid of one bias point.  Real axis: n_real nodes E, weights w, occupations
+ * fS = f(E - mu_S), fD = f(E - mu_D), broadening eta (energies E + i eta).  Contour:
+ * n_cont nodes z (complex, Im z > 0) and complex weights c such that
+ *   integral_{E_B}^{E_min} G(E) f(E - mu_min) dE = - sum_k c_k G(z_k).
+ * The electron count of ring r is
+ *   n_r = (g_s g_b/pi) Im sum_k c_k Tr_r G(z_k)
+ *       + (g_s g_b/2pi) sum_k w_k [fS_k Tr_r A_S(E_k) + fD_k Tr_r A_D(E_k)]. */
+typedef struct {
+  int n_real;
+  const double* E;
+  const double* w;
+  const double* fS;
+  const double* fD;
+  double eta;
+  int n_cont;
+  const double* z;
+  const double* c;
+} negf_grid;
+int negf_set_grid(negf_ctx* ctx, int dev, const negf_grid* grid);
+
+/* Default grid of a bias point (Eq. Rho, Sec. 3.3).  Real axis on [E_min, E_max] with
+ * E_min = mu_min - f1 kT and E_max = mu_max + f2 kT unless given (pass NaN for the
+ * default), by `rule`.  Contour: Gauss-Legendre in theta on the upper semicircle over
+ * [E_B, E_min], c_k = W_k z'(theta_k) f(z_k - mu_min).  E_B must lie below every band. */
+typedef struct {
+  double mu_S, mu_D, kT, eta;
+  double E_B, E_min, E_max, f1, f2;
+  int n_real, n_cont, rule;
+} negf_grid_spec;
+
+/* Host helper: fill caller arrays E, w, fS, fD (n_real each) and z, c (2*n_cont each). */
+int negf_make_grid(const negf_grid_spec* spec, double* E, double* w, double* fS, double* fD,
+                   double* z, double* c);
+/* Build the default grid and set it on a device. */
+int negf_set_grid_spec(negf_ctx* ctx, int dev, const negf_grid_spec* spec);
+
+/* ---- one NEGF evaluation ----------------------------------------------------------------- */
+
+/* Outputs of one device.  n (n_rings, required): electron count per ring.  T (n_real,
+ * optional): sum over chains of g_b T_chain(E).  I (1, optional): Landauer current
+ * I = g_s (e^2/h) sum_k w_k T(E_k) (fS_k - fD_k).  n_cont / n_real_part (n_rings,
+ * optional): the two parts of n.  flags (n_real, optional, int): per-energy precision
+ * flags of the mixed path (1 = recomputed in FP64).  resid (n_real, optional): per-energy
+ * sum-rule residual of the sweep that produced the result.  Any pointer may be NULL
+ * except n.  If on_device != 0 every pointer is device memory on the context's GPU and
+ * the results are left there (no host copy). */
+typedef struct {
+  double* n;
+  double* T;
+  double* I;
+  double* n_cont;
+  double* n_real_part;
+  int* flags;
+  double* resid;
+  int on_device;
+} negf_out;
+
+/* Evaluate n_devs devices in one persistent launch (every (device, chain, energy) lane
+ * of the batch, scheduled by the autotuned plan).  outs[i] receives device devs[i].
+ * Results of a device are bitwise the same alone and inside any batch. */
+int negf_compute(negf_ctx* ctx, const int* devs, int n_devs, negf_out* outs);
+
+/* Per-energy ring traces for sampled checks of one device: for the real-axis energies
+ * listed in idx_real (count k_real) Tr_r A_S and Tr_r A_D (k_real x n_rings each, summed
+ * over chains, without degeneracy factors), and for contour nodes idx_cont (count k_cont)
+ * Tr_r G (k_cont x n_rings complex).  Same kernels as negf_compute. */
+int negf_sample_lanes(negf_ctx* ctx, int dev, int k_real, const int* idx_real, double* AS,
+                      double* AD, int k_cont, const int* idx_cont, double* G);
+
+/* Neutral reference electron count n0 per ring (Sec. 2.2.1, rho_0 with E_l = E_u = 0):
+ * contour over [E_B, 0] with occupation 1 and zero potential in the device and leads. */
+int negf_neutral_charge(negf_ctx* ctx, int dev, int n_cont, double E_B, double* n0);
+
+/* ---- self-consistent loop (Alg. 3) with the 1D Poisson stand-in ------------------------ */
+
+/* Poisson stand-in, one node per ring:
+ *   U_i - U_G - (lam/dx)^2 (U_{i+1} - 2 U_i + U_{i-1}) = kappa (n_i - n0_i),
+ * Dirichlet U_{-1} = U_S, U_N = U_D, U_G = phi_gate - V_GS.  kappa (eV per electron) of a
+ * coaxial gate: negf_poisson_kappa. */
+typedef struct {
+  double kappa, dx_nm, lam_nm, phi_gate;
+} negf_poisson;
+double negf_poisson_kappa(double eps_r, double d_nm, double t_ox_nm, double dx_nm);
+
+/* Bias point: lead potentials U_S = 0, U_D = -V_DS; mu_S = 0, mu_D = -V_DS. */
+typedef struct {
+  double V_DS, V_GS;
+} negf_bias;
+
+/* Broyden's modified second method: fraction zeta, history M (also the iteration limit),
+ * tolerance on eps_max = max_i |n_in - n_out| / (n_in + n_out). */
+typedef struct {
+  double zeta;
+  int M;
+  double tol;
+} negf_broyden;
+
+/* Result of a solve.  n, U (n_rings), T (n_real), history (M) are caller arrays (NULL to
+ * skip); converged, iterations, I are written. */
+typedef struct {
+  double* n;
+  double* U;
+  double* T;
+  double* history;
+  double I;
+  int converged;
+  int iterations;
+} negf_sc_result;
+
+/* Self-consistent solve of one device at one bias point, starting from potential U0
+ * (n_rings): n_in = the charge whose Poisson solution is U0; then repeat
+ * U = Poisson(n_in) -> n_out = NEGF(U) -> Broyden until eps_max < tol or M evaluations.
+ * The grid of the device must already match the bias (negf_set_grid_spec).  The loop runs
+ * on the device (one captured CUDA graph per iteration); the host reads one flag per
+ * iteration.  Returns NEGF_ENOTCONVERGED (with the result filled) if the limit is hit. */
+int negf_sc_solve(negf_ctx* ctx, int dev, const negf_bias* bias, const negf_poisson* pois,
+                  const negf_broyden* br, const double* U0, negf_sc_result* res);
+
+/* Stateful form of the same loop, for callers that interleave work or checkpoint.
+ * negf_sc_begin: as negf_sc_solve up to the first iteration (bias, n0, starting charge,
+ * Broyden state, captured graph); the device then refuses set-up calls (NEGF_EBUSY) until
+ * negf_sc_end.  negf_sc_step: run k iterations; with state != NULL the host waits after
+ * each one and stops early once it is nonzero (1 converged, 2 history exhausted); with
+ * state == NULL the k iterations are only enqueued (iterations after convergence leave the
+ * result unchanged).  negf_sc_end: wait, fill res (may be NULL), free the session; returns
+ * NEGF_ENOTCONVERGED if res is given and the loop did not converge.
+ * negf_sc_get_state / negf_sc_set_state: the Broyden state (n_in, n_in_old, f_old:
+ * n_rings each; V, W: M x n_rings each, row j = column j of Alg. 3's V^T / W; m) for
+ * checkpoint and warm start (Sec. 3.3 starts each V_gs from the previous solution). */
+int negf_sc_begin(negf_ctx* ctx, int dev, const negf_bias* bias, const negf_poisson* pois,
+                  const negf_broyden* br, const double* U0);
+int negf_sc_step(negf_ctx* ctx, int dev, int k, int* state);
+int negf_sc_end(negf_ctx* ctx, int dev, negf_sc_result* res);
+int negf_sc_get_state(negf_ctx* ctx, int dev, double* n_in, double* n_in_old, double* f_old,
+                      double* V, double* W, int* m);
+int negf_sc_set_state(negf_ctx* ctx, int dev, const double* n_in, const double* n_in_old,
+                      const double* f_old, const double* V, const double* W, int m);
+
+/* ---- diagnostics ---------------------------------------------------------------------- */
+
+/* Number of kernel launches the context issued since creation (for accounting). */
+int negf_launch_count(const negf_ctx* ctx, uint64_t* launches);
+
+/* Kernel timing: with profiling on, every batched sweep issued outside graph capture is
+ * bracketed by CUDA events on the context's stream; negf_kernel_time waits for them and
+ * returns (and resets) the summed sweep time in ms and the number of timed sweeps. */
+int negf_profile(negf_ctx* ctx, int enable);
+int negf_kernel_time(negf_ctx* ctx, double* sweep_ms, uint64_t* sweeps);
+
+/* Measured FP64 FMA throughput of this GPU (TFLOP/s): a register-resident FMA loop over
+ * every SM, best of three, for the FP64 roofline of the sweep kernels. */
+int negf_fp64_peak(negf_ctx* ctx, double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEGF_H */

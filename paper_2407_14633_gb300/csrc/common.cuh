@@ -1,0 +1,206 @@
+// Shared declarations of the NEGF CUDA library: complex arithmetic, the device views the
+// kernels read, work items of the batched sweep, and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace negf {
+
+// ---------------------------------------------------------------- complex arithmetic
+template <typename T>
+struct cx {
+  T re, im;
+};
+using cd = cx<double>;
+using cf = cx<float>;
+
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> mk(T r, T i) {
+  cx<T> z;
+  z.re = r;
+  z.im = i;
+  return z;
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> scale(cx<T> a, T s) { return mk(a.re * s, a.im * s); }
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> conjg(cx<T> a) { return mk(a.re, -a.im); }
+template <typename T>
+__host__ __device__ __forceinline__ T abs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+// acc + a * b with fused multiply-adds (4 FMA)
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a) * b
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmac_cj(cx<T> acc, cx<T> a, cx<T> b) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+// 1 / a = conj(a) / |a|^2
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> crecip(cx<T> a) {
+  T s = T(1) / fma(a.re, a.re, a.im * a.im);
+  return mk(a.re * s, -a.im * s);
+}
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cvt(cd a);
+template <>
+__host__ __device__ __forceinline__ cd cvt<double>(cd a) { return a; }
+template <>
+__host__ __device__ __forceinline__ cf cvt<float>(cd a) { return mk((float)a.re, (float)a.im); }
+
+// ---------------------------------------------------------------- limits
+constexpr int MAX_BLOCK = 64;     // widest ring block
+constexpr int MAX_LEAD = 64;      // widest lead ring
+constexpr int LANES = 32;         // energies per warp item of the thread-per-lane sweep
+
+// ---------------------------------------------------------------- device-side views
+// One lead of one chain: the closed-form surface Green's function of every angular mode j
+// needs a1_j = |lambda_j(T1)|^2, a2_j = |lambda_j(T2)|^2 and at_j = |lambda_j(tau)|^2.
+struct LeadView {
+  int m;            // sites of the lead ring
+  double U;         // lead potential energy
+  const double* a1; // m
+  const double* a2; // m
+  const double* at; // m
+  const int* sites; // m site indices inside the boundary layer
+  const double* tw; // 2m: cos, sin of 2 pi k / m (k = 0..m-1), interleaved
+};
+
+// One chain of one device.
+struct ChainView {
+  const cd* Hdiag;  // L*b*b, without potential
+  const cd* Hup;    // (L-1)*b*b
+  // padded sparse forms of H_{l,l+1}: row r: rs_cnt[l*b+r] entries (col rs_idx, val rs_val)
+  // and column c: cs_cnt (row cs_idx, val cs_val); kmax entries per row/column
+  const int* rs_cnt;
+  const int* rs_idx;
+  const cd* rs_val;
+  const int* cs_cnt;
+  const int* cs_idx;
+  const cd* cs_val;
+  int kmax;
+  const double* hsq; // block 1: |H_{l,l+1}|^2 per layer (L-1)
+  double g_b;
+  LeadView lead[2];
+};
+
+struct DeviceView {
+  int n_rings, L, b, rpb, n_chains;
+  const double* U;        // n_rings potential energy per ring
+  // real-axis grid
+  int n_real;
+  const double* E;
+  const double* w;
+  const double* fS;
+  const double* fD;
+  double eta;
+  // contour grid
+  int n_cont;
+  const cd* z;
+  const cd* c;
+  ChainView ch[8];        // up to 8 chains (modes)
+};
+
+// A work item of the sweep: one warp handles up to LANES energies (thread-per-lane kernels)
+// or one energy (warp-per-lane kernels) of one (device, chain, kind).
+struct WorkItem {
+  int dev;        // index into the DeviceView array of the launch
+  int chain;
+  int kind;       // 0 real axis, 1 contour
+  int e0;         // first energy index of the kind
+  int ne;         // number of energies
+  int pad;
+  long long part; // offset of this item's per-ring partial sums (n_rings doubles)
+  long long tout; // offset of its T(E) outputs (real items) in the T-partial buffer
+};
+
+struct SweepArgs {
+  const DeviceView* devs;
+  const WorkItem* items;
+  const int* order;       // schedule order of items (longest first)
+  int n_items;
+  int* counter;           // persistent-scheduling counter (zeroed before launch)
+  double* partial;        // per-item per-ring partial sums
+  double* Tpart;          // per-chain T(E)
+  double* resid;          // per-lane sum-rule residual (may be null)
+  unsigned char* stage;   // staging of the forward sweep, per resident warp
+  long long stage_stride; // bytes per resident warp
+  int* status;            // device error flag (0 ok)
+};
+
+// ---------------------------------------------------------------- launchers
+// thread-per-lane sweep of 1x1 blocks (every chain of every item has b == 1)
+int launch_sweep_b1_f64(const SweepArgs& a, int grid, int block, cudaStream_t s);
+int launch_sweep_b1_f32(const SweepArgs& a, int grid, int block, cudaStream_t s);
+// thread-per-lane sweep of 2x2 blocks
+int launch_sweep_b2_f64(const SweepArgs& a, int grid, int block, cudaStream_t s);
+// warp-per-lane sweep of b x b blocks (b <= MAX_BLOCK) with smem matrices
+int launch_sweep_blk_f64(const SweepArgs& a, int b_max, int m_max, int grid, int warps,
+                         cudaStream_t s);
+__host__ __device__ size_t sweep_blk_smem_bytes(int b, int m, int warps);
+// resident CTAs per SM of a sweep kernel (sets the dynamic shared memory limit first)
+int sweep_chain_occupancy(int cls, int threads, size_t smem);
+int sweep_blk_occupancy(int warps, size_t smem);
+
+struct ReduceDev {
+  int n_rings, n_real, n_chains;
+  int it0, it1;           // item range of the device
+  const WorkItem* items;
+  const double* partial;
+  const double* Tpart;    // n_chains x n_real (base of the device)
+  const double* g_b;      // per chain (device array)
+  const double* w;
+  const double* fS;
+  const double* fD;
+  double* n;              // outputs (device)
+  double* n_real_part;
+  double* n_cont;
+  double* T;
+  double* I;
+};
+int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s);
+
+// per-layer potential added to diagonal blocks is applied inside the sweep kernels.
+
+// self-consistency kernels
+struct ScDev {
+  int N, M;
+  double zeta, tol, kappa, r, U_G, U_S, U_D;
+  double* n_in;      // N
+  double* n_in_old;  // N
+  double* f_old;     // N
+  double* V;         // M x N
+  double* W;         // M x N (column j of W stored as row j)
+  double* n0;        // N
+  double* U;         // N (Poisson output -> sweep input)
+  const double* n_out; // N (sweep output)
+  double* hist;      // M
+  int* m;            // Broyden counter
+  int* state;        // 0 running, 1 converged, 2 limit reached
+  double* cp;        // N scratch (Thomas)
+};
+int launch_broyden(const ScDev* devs, int n, cudaStream_t s);
+int launch_poisson(const ScDev* devs, int n, cudaStream_t s);
+
+// host quadrature helper: the upper semicircle contour over [E_B, E_end]
+void contour_arc(double E_B, double E_end, int n, double* z, double* zw);
+
+}  // namespace negf

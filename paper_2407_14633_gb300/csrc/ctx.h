@@ -1,0 +1,143 @@
+// Host-side state of the NEGF library: context, device arena, devices.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/negf.h"
+#include "common.cuh"
+
+namespace negf {
+
+// A device allocation owned by a context; freed with it.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Arena {
+  size_t used = 0, budget = 0, peak = 0;
+  long long allocs = 0;
+  int fail_after = 0;  // host-side fault injection: the n-th allocation fails
+  std::string err;
+  bool alloc(DBuf& b, size_t bytes);
+  void release(DBuf& b);
+};
+
+struct HostLead {
+  int m = 0;
+  double U = 0.0;
+  std::vector<double> T1, T2, tau;  // first rows, 2m each
+  std::vector<int> sites;
+  bool set = false;
+};
+
+struct ChainData {
+  std::vector<double> Hdiag, Hup;  // interleaved complex
+  double g_b = 1.0;
+  bool h_set = false;
+  HostLead lead[2];
+  // device copies
+  DBuf dHdiag, dHup, dcs_cnt, dcs_idx, dcs_val, dhsq;
+  DBuf da1[2], da2[2], dat[2], dsites[2], dtw[2];
+  int kmax = 0;
+};
+
+// Device scratch of one launch plan.  The context owns one for ad-hoc evaluations; a
+// self-consistent session owns its own, so its captured graph never sees a buffer that a
+// later call reallocated.
+struct PlanBufs {
+  DBuf views, items, order, counter, partial, tpart, stage, reduce, status;
+};
+
+struct ScSession;
+
+struct Dev {
+  int n_rings = 0, block = 1, rpb = 1, n_chains = 1, L = 0;
+  std::vector<ChainData> ch;
+  std::vector<double> U;
+  bool u_set = false;
+  // grid (host copies) and spec
+  int n_real = 0, n_cont = 0;
+  double eta = 0.0;
+  bool grid_set = false;
+  bool spec_set = false;
+  negf_grid_spec spec{};
+  // device buffers
+  DBuf dU, dE, dw, dfS, dfD, dz, dc, dgb;
+  DBuf dn, dnr, dnc, dT, dI;
+  ScSession* sc = nullptr;   // active self-consistent session (sc.cu)
+};
+
+struct Ctx {
+  int ordinal = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  negf_opts opts{};
+  int sms = 0;
+  Arena arena;
+  std::map<int, std::unique_ptr<Dev>> devs;
+  int next_dev = 1;
+  std::string last_error;
+  uint64_t launches = 0;
+  // scratch of ad-hoc batched sweeps, grown on demand
+  PlanBufs scratch;
+  // kernel timing (negf_profile): event pairs around sweep launches outside graph capture
+  bool profile = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+  double prof_ms = 0.0;
+  uint64_t prof_count = 0;
+  // serving state (serve.cu)
+  struct Serve* serve = nullptr;
+  std::mutex serve_mu;
+};
+
+struct Serve;
+void serve_free(Ctx* c);
+int set_err(Ctx* c, int code, const std::string& msg);
+bool ensure(Ctx* c, DBuf& b, size_t bytes);
+int upload(Ctx* c, DBuf& b, const void* src, size_t bytes);
+
+// Compute one NEGF evaluation of a list of devices with optional view overrides.
+struct ViewOverride {
+  const double* U = nullptr;       // device pointer replacing the potential
+  bool zero_lead_U = false;        // leads at zero potential
+  // replacement grid (device pointers); n_real < 0 keeps the device grid
+  int n_real = -1;
+  const double *E = nullptr, *w = nullptr, *fS = nullptr, *fD = nullptr;
+  double eta = 0.0;
+  int n_cont = -1;
+  const cd *z = nullptr, *c = nullptr;
+  bool one_energy_per_item = false;
+};
+struct Plan {
+  PlanBufs* bufs = nullptr;
+  std::vector<Dev*> devs;
+  std::vector<DeviceView> views;
+  std::vector<WorkItem> items;
+  std::vector<int> it0;
+  int n_items = 0, bmax = 1, mmax = 1, block_threads = 256, blk_warps = 1;
+  int grid[3] = {0, 0, 0}, ooff[3] = {0, 0, 0}, ncls[3] = {0, 0, 0};
+  long long stride[3] = {0, 0, 0};
+  long long tpos = 0;
+};
+int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOverride>* ov, int chain_only,
+               Plan& P, PlanBufs* bufs = nullptr);
+void free_plan_bufs(Ctx* c, PlanBufs& b);
+void sc_session_free(Ctx* c, Dev* d);
+int launch_plan(Ctx* c, const Plan& P);
+int copy_out(Ctx* c, const Plan& P, const negf_out* outs);
+int check_ready(Ctx* c, Dev* d);
+Dev* find_device(Ctx* c, int dev);
+int compute_batch(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOverride>* ov,
+                  std::vector<double*>* n_out, bool sync_copy, const negf_out* outs);
+DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o);
+
+}  // namespace negf
+
+struct negf_ctx : public negf::Ctx {};

@@ -1,0 +1,53 @@
+// Second stage of the energy quadrature (Eq. Rho, Eq. deviceCharacteristics): per device,
+// sum the per-item partial ring sums in item order (deterministic, independent of the
+// schedule and of the rest of the batch), sum T(E) over chains with their band
+// degeneracy, and reduce the Landauer current I = g_s (e^2/h) sum_k w_k T_k (fS_k - fD_k)
+// with a fixed-shape tree in shared memory.
+#include "common.cuh"
+
+namespace negf {
+
+// e^2/h in A/V from the exact SI 2019 elementary charge and Planck constant
+__constant__ double kE2H = 1.602176634e-19 * 1.602176634e-19 / 6.62607015e-34;
+
+__global__ void __launch_bounds__(256) reduce_kernel(const ReduceDev* devs) {
+  const ReduceDev& R = devs[blockIdx.x];
+  __shared__ double sh[256];
+  // ring sums: real-axis items and contour items separately
+  for (int r = threadIdx.x; r < R.n_rings; r += blockDim.x) {
+    double sr = 0.0, sc = 0.0;
+    for (int it = R.it0; it < R.it1; ++it) {
+      const WorkItem& W = R.items[it];
+      const double v = R.partial[W.part + r];
+      if (W.kind == 0)
+        sr += v;
+      else
+        sc += v;
+    }
+    R.n[r] = sr + sc;
+    if (R.n_real_part) R.n_real_part[r] = sr;
+    if (R.n_cont) R.n_cont[r] = sc;
+  }
+  // T(E) and the current
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < R.n_real; k += blockDim.x) {
+    double t = 0.0;
+    for (int c = 0; c < R.n_chains; ++c) t += R.g_b[c] * R.Tpart[(long long)c * R.n_real + k];
+    if (R.T) R.T[k] = t;
+    acc += R.w[k] * t * (R.fS[k] - R.fD[k]);
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && R.I) *R.I = 2.0 * kE2H * sh[0];
+}
+
+int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s) {
+  reduce_kernel<<<n_devs, 256, 0, s>>>(devs);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace negf

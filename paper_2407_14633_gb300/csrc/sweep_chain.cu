@@ -1,0 +1,385 @@
+// Thread-per-lane recursive Green's function sweeps for narrow blocks (b = 1, 2).
+//
+// One warp takes a work item of up to 32 energies of one (device, chain, kind); each
+// thread runs the whole forward and backward sweep of its energy (the paper's Alg. 2
+// recursion done per energy, Sec. 2.2.4 "future work": store the per-energy recursion
+// vectors instead of recomputing them).  The forward quantities are staged per resident
+// warp in global memory, interleaved [layer][field][lane] so every warp access is one
+// coalesced 256-byte line.  Per-ring contributions of the 32 energies are reduced through
+// a 32 x 33 shared-memory transpose (one add per ring and lane, fixed order) into the
+// item's partial sums; the second stage (reduce.cu) sums items in item order, so results
+// do not depend on how items are scheduled or batched.
+//
+// b = 1 (mode space): with scalar blocks the lead columns need only moduli,
+//   q_l = |G_{l,0}|^2 / |G_{l,l}|^2 = |h_{l-1}|^2 |gL_{l-1}|^2 q_{l-1},  q_0 = 1,
+//   c_l = |G_{l,L-1}|^2 = |gL_l|^2 |h_l|^2 c_{l+1},  c_{L-1} = |G_{L-1,L-1}|^2,
+//   G_{l,l} = gL_l + gL_l^2 |h_l|^2 G_{l+1,l+1},
+//   A_S,ll = Gamma_S q_l |G_ll|^2, A_D,ll = Gamma_D c_l, T = Gamma_S Gamma_D c_0.
+#include "common.cuh"
+#include "lead.cuh"
+
+namespace negf {
+
+namespace {
+
+__device__ __forceinline__ int next_item(int* counter, int lane) {
+  int it = 0;
+  if (lane == 0) it = atomicAdd(counter, 1);
+  return __shfl_sync(0xffffffffu, it, 0);
+}
+
+// flush ring slots [base, base + count) of the 32 x 33 transpose buffer into `dst`
+__device__ __forceinline__ void flush_rings(double* red, int lane, int count, double* dst) {
+  __syncwarp();
+  if (lane < count) {
+    double s = 0.0;
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) s += red[lane * 33 + j];
+    dst[lane] = s;
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> ld_c(const unsigned char* p) {
+  return *reinterpret_cast<const cx<T>*>(p);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ b = 1
+template <typename T>
+__global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
+  extern __shared__ double sm_b1[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  double* red = sm_b1 + wib * (32 * 33);
+  T* st = reinterpret_cast<T*>(a.stage + (long long)gw * a.stage_stride);
+
+  for (;;) {
+    const int it = next_item(a.counter, lane);
+    if (it >= a.n_items) break;
+    const WorkItem W = a.items[a.order[it]];
+    const DeviceView& D = a.devs[W.dev];
+    const ChainView& C = D.ch[W.chain];
+    const int L = D.L;
+    const bool act = lane < W.ne;
+    const int k = W.e0 + (act ? lane : 0);
+    const double g = 2.0 * C.g_b;
+    double* part = a.partial + W.part;
+
+    cd eps;
+    double wS = 0.0, wD = 0.0;     // real axis: g w f / (2 pi)
+    cd kap = mk(0.0, 0.0);         // contour: (g / pi) c_k
+    if (W.kind == 0) {
+      eps = mk(D.E[k], D.eta);
+      if (act) {
+        wS = g * D.w[k] * D.fS[k] * (0.5 / 3.14159265358979323846);
+        wD = g * D.w[k] * D.fD[k] * (0.5 / 3.14159265358979323846);
+      }
+    } else {
+      eps = D.z[k];
+      if (act) kap = scale(D.c[k], g / 3.14159265358979323846);
+    }
+    // contact self-energies in FP64
+    const cd sS = mode_sigma(C.lead[0], 0, eps);
+    const cd sD = mode_sigma(C.lead[1], 0, eps);
+    const double gamS = -2.0 * sS.im, gamD = -2.0 * sD.im;
+
+    const cx<T> e = mk((T)eps.re, (T)eps.im);
+    const cx<T> SS = mk((T)sS.re, (T)sS.im), SD = mk((T)sD.re, (T)sD.im);
+    const double* U = D.U;
+    const cd* Hd = C.Hdiag;
+    const double* hsq = C.hsq;
+
+    // ---------------- forward sweep
+    cx<T> gl = mk(T(0), T(0));
+    T rl = T(0);              // |gL_l|^2
+    T ql = (T)(wS * gamS);    // (g w fS / 2pi) Gamma_S |Q_l|^2
+    const int nf = (W.kind == 0) ? 4 : 2;
+    for (int l = 0; l < L; ++l) {
+      const cd h = Hd[l];
+      cx<T> x = mk((T)(eps.re - h.re - U[l]), (T)(eps.im - h.im));
+      (void)e;
+      if (l == 0) x = x - SS;
+      if (l == L - 1) x = x - SD;
+      if (l > 0) {
+        const T hs = (T)hsq[l - 1];
+        x.re = fma(-hs, gl.re, x.re);
+        x.im = fma(-hs, gl.im, x.im);
+        if (W.kind == 0) ql = hs * rl * ql;
+      }
+      const T r = T(1) / fma(x.re, x.re, x.im * x.im);
+      gl = mk(x.re * r, -x.im * r);
+      rl = r;
+      T* s = st + (long long)l * nf * 32;
+      s[lane] = gl.re;
+      s[32 + lane] = gl.im;
+      if (W.kind == 0) {
+        s[64 + lane] = r;
+        s[96 + lane] = ql;
+      }
+    }
+
+    // ---------------- backward sweep
+    cx<T> G = gl;             // G_{L-1,L-1}
+    T c = abs2(G);            // |G_{l,L-1}|^2
+    for (int l = L - 1; l >= 0; --l) {
+      const T* s = st + (long long)l * nf * 32;
+      if (l < L - 1) {
+        const cx<T> gll = mk(s[lane], s[32 + lane]);
+        const T hs = (T)hsq[l];
+        cx<T> t = scale(gll * G, hs);        // |h|^2 gL G_{l+1}
+        G = cmac(gll, gll, t);               // gL + gL (|h|^2 gL G_{l+1})
+        if (W.kind == 0) c = s[64 + lane] * hs * c;
+      }
+      double v;
+      if (W.kind == 0) {
+        const T q = s[96 + lane];
+        v = (double)(q * abs2(G)) + wD * gamD * (double)c;
+      } else {
+        v = kap.re * (double)G.im + kap.im * (double)G.re;
+      }
+      red[(l & 31) * 33 + lane] = v;
+      if ((l & 31) == 0) {
+        const int cnt = min(32, L - l);
+        flush_rings(red, lane, cnt, part + l);
+      }
+    }
+    if (W.kind == 0 && act) a.Tpart[W.tout + lane] = gamS * gamD * (double)c;
+  }
+}
+
+// ------------------------------------------------------------------ b = 2
+// 2 x 2 layers with the leads on one site each (unit cells of two mode-space rings).
+template <typename T>
+struct m2 {
+  cx<T> a[2][2];
+};
+
+template <typename T>
+__device__ __forceinline__ m2<T> mul2(const m2<T>& A, const m2<T>& B) {
+  m2<T> C;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) C.a[i][j] = cmac(A.a[i][0] * B.a[0][j], A.a[i][1], B.a[1][j]);
+  return C;
+}
+template <typename T>
+__device__ __forceinline__ m2<T> inv2(const m2<T>& A) {
+  cx<T> det = A.a[0][0] * A.a[1][1] - A.a[0][1] * A.a[1][0];
+  cx<T> id = crecip(det);
+  m2<T> B;
+  B.a[0][0] = A.a[1][1] * id;
+  B.a[1][1] = A.a[0][0] * id;
+  B.a[0][1] = mk(T(0), T(0)) - A.a[0][1] * id;
+  B.a[1][0] = mk(T(0), T(0)) - A.a[1][0] * id;
+  return B;
+}
+template <typename T>
+__device__ __forceinline__ m2<T> load2(const cd* p, bool dagger) {
+  m2<T> M;
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      cd v = dagger ? conjg(p[j * 2 + i]) : p[i * 2 + j];
+      M.a[i][j] = mk((T)v.re, (T)v.im);
+    }
+  return M;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
+  extern __shared__ double sm_b2[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  double* red = sm_b2 + wib * (32 * 33);
+  T* st = reinterpret_cast<T*>(a.stage + (long long)gw * a.stage_stride);
+  constexpr int NF = 12;  // gL (8 reals) + R (4 reals)
+
+  for (;;) {
+    const int it = next_item(a.counter, lane);
+    if (it >= a.n_items) break;
+    const WorkItem W = a.items[a.order[it]];
+    const DeviceView& D = a.devs[W.dev];
+    const ChainView& C = D.ch[W.chain];
+    const int L = D.L;
+    const bool act = lane < W.ne;
+    const int k = W.e0 + (act ? lane : 0);
+    const double g = 2.0 * C.g_b;
+    double* part = a.partial + W.part;
+
+    cd eps;
+    double wS = 0.0, wD = 0.0;
+    cd kap = mk(0.0, 0.0);
+    if (W.kind == 0) {
+      eps = mk(D.E[k], D.eta);
+      if (act) {
+        wS = g * D.w[k] * D.fS[k] * (0.5 / 3.14159265358979323846);
+        wD = g * D.w[k] * D.fD[k] * (0.5 / 3.14159265358979323846);
+      }
+    } else {
+      eps = D.z[k];
+      if (act) kap = scale(D.c[k], g / 3.14159265358979323846);
+    }
+    const cd sS = mode_sigma(C.lead[0], 0, eps);
+    const cd sD = mode_sigma(C.lead[1], 0, eps);
+    const int siteS = C.lead[0].sites[0], siteD = C.lead[1].sites[0];
+    const int rpb = D.rpb;
+    const double gamS = -2.0 * sS.im, gamD = -2.0 * sD.im;
+    const T lS = (T)sqrt(fmax(gamS, 0.0)), lD = (T)sqrt(fmax(gamD, 0.0));
+    const double* U = D.U;
+
+    // forward: gL_l and R_l = Q_l L_S (a 2-vector, L_S = sqrt(Gamma_S) e_siteS)
+    m2<T> gl;
+    cx<T> R[2];
+    for (int l = 0; l < L; ++l) {
+      m2<T> A = load2<T>(C.Hdiag + (long long)l * 4, false);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) A.a[i][j] = mk(T(0), T(0)) - A.a[i][j];
+      // ring of site a: 2l + a for unit cells (rpb = 2), l for a two-site ring (rpb = 1)
+      const int ring0 = l * rpb, ring1 = l * rpb + (rpb - 1);
+      A.a[0][0] = A.a[0][0] + mk((T)(eps.re - U[ring0]), (T)eps.im);
+      A.a[1][1] = A.a[1][1] + mk((T)(eps.re - U[ring1]), (T)eps.im);
+      if (l == 0) A.a[siteS][siteS] = A.a[siteS][siteS] - mk((T)sS.re, (T)sS.im);
+      if (l == L - 1) A.a[siteD][siteD] = A.a[siteD][siteD] - mk((T)sD.re, (T)sD.im);
+      cx<T> Rn[2];
+      if (l > 0) {
+        const cd* hu = C.Hup + (long long)(l - 1) * 4;
+        m2<T> X = mul2(load2<T>(hu, true), gl);      // H_{l,l-1} gL_{l-1}
+        m2<T> Y = mul2(X, load2<T>(hu, false));      // ... H_{l-1,l}
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) A.a[i][j] = A.a[i][j] - Y.a[i][j];
+        if (W.kind == 0) {
+#pragma unroll
+          for (int i = 0; i < 2; ++i) Rn[i] = cmac(X.a[i][0] * R[0], X.a[i][1], R[1]);
+        }
+      } else {
+        Rn[0] = mk(T(0), T(0));
+        Rn[1] = mk(T(0), T(0));
+        Rn[siteS] = mk(lS, T(0));
+      }
+      gl = inv2(A);
+      R[0] = Rn[0];
+      R[1] = Rn[1];
+      T* s = st + (long long)l * NF * 32;
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          s[((i * 2 + j) * 2) * 32 + lane] = gl.a[i][j].re;
+          s[((i * 2 + j) * 2 + 1) * 32 + lane] = gl.a[i][j].im;
+        }
+      if (W.kind == 0) {
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          s[(8 + 2 * i) * 32 + lane] = R[i].re;
+          s[(9 + 2 * i) * 32 + lane] = R[i].im;
+        }
+      }
+    }
+
+    // backward: G_ll, K_l = G_{l,L-1} L_D, P_l = G_ll R_l
+    m2<T> G = gl;
+    cx<T> K[2];
+    K[0] = scale(G.a[0][siteD], lD);
+    K[1] = scale(G.a[1][siteD], lD);
+    for (int l = L - 1; l >= 0; --l) {
+      const T* s = st + (long long)l * NF * 32;
+      if (l < L - 1) {
+        m2<T> gll;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+            gll.a[i][j] = mk(s[((i * 2 + j) * 2) * 32 + lane], s[((i * 2 + j) * 2 + 1) * 32 + lane]);
+        const cd* hu = C.Hup + (long long)l * 4;
+        m2<T> Z = mul2(gll, load2<T>(hu, false));     // gL_l H_{l,l+1}
+        m2<T> Wm = mul2(Z, G);
+        m2<T> Y = mul2(load2<T>(hu, true), gll);      // H_{l+1,l} gL_l
+        m2<T> WY = mul2(Wm, Y);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) G.a[i][j] = gll.a[i][j] + WY.a[i][j];
+        if (W.kind == 0) {
+          cx<T> Kn[2];
+#pragma unroll
+          for (int i = 0; i < 2; ++i) Kn[i] = cmac(Z.a[i][0] * K[0], Z.a[i][1], K[1]);
+          K[0] = Kn[0];
+          K[1] = Kn[1];
+        }
+      }
+      double v0, v1;
+      if (W.kind == 0) {
+        cx<T> Rl[2];
+        Rl[0] = mk(s[8 * 32 + lane], s[9 * 32 + lane]);
+        Rl[1] = mk(s[10 * 32 + lane], s[11 * 32 + lane]);
+        cx<T> P0 = cmac(G.a[0][0] * Rl[0], G.a[0][1], Rl[1]);
+        cx<T> P1 = cmac(G.a[1][0] * Rl[0], G.a[1][1], Rl[1]);
+        v0 = wS * (double)abs2(P0) + wD * (double)abs2(K[0]);
+        v1 = wS * (double)abs2(P1) + wD * (double)abs2(K[1]);
+      } else {
+        v0 = kap.re * (double)G.a[0][0].im + kap.im * (double)G.a[0][0].re;
+        v1 = kap.re * (double)G.a[1][1].im + kap.im * (double)G.a[1][1].re;
+      }
+      // rings of the layer -> transpose slots ring & 31
+      const int r0 = l * rpb;
+      if (rpb == 2) {
+        red[(r0 & 31) * 33 + lane] = v0;
+        red[((r0 + 1) & 31) * 33 + lane] = v1;
+      } else {
+        red[(r0 & 31) * 33 + lane] = v0 + v1;
+      }
+      if ((r0 & 31) == 0) {
+        const int cnt = min(32, D.n_rings - r0);
+        flush_rings(red, lane, cnt, part + r0);
+      }
+    }
+    if (W.kind == 0 && act) {
+      // T = Tr[Gamma_S G_{0,L-1} Gamma_D G_{0,L-1}^dag] = Gamma_S |K_0[siteS]|^2
+      a.Tpart[W.tout + lane] = gamS * (double)abs2(K[siteS]);
+    }
+  }
+}
+
+static int launch_common(void (*kern)(SweepArgs), const SweepArgs& a, int grid, int block,
+                         cudaStream_t s) {
+  // the dynamic shared memory limit was raised by sweep_chain_occupancy when planning
+  const size_t smem = (size_t)(block / 32) * 32 * 33 * sizeof(double);
+  kern<<<grid, block, smem, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_sweep_b1_f64(const SweepArgs& a, int grid, int block, cudaStream_t s) {
+  return launch_common(sweep_b1_kernel<double>, a, grid, block, s);
+}
+int launch_sweep_b1_f32(const SweepArgs& a, int grid, int block, cudaStream_t s) {
+  return launch_common(sweep_b1_kernel<float>, a, grid, block, s);
+}
+int launch_sweep_b2_f64(const SweepArgs& a, int grid, int block, cudaStream_t s) {
+  return launch_common(sweep_b2_kernel<double>, a, grid, block, s);
+}
+
+}  // namespace negf
+
+namespace negf {
+int sweep_chain_occupancy(int cls, int threads, size_t smem) {
+  void (*k)(SweepArgs) = cls == 0 ? sweep_b1_kernel<double> : sweep_b2_kernel<double>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem) != cudaSuccess || per < 1) {
+    cudaGetLastError();
+    per = 1;
+  }
+  return per;
+}
+}  // namespace negf

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every symbol include/negf.h declares; host
+logic that needs no GPU (grid helper, Poisson constant, status strings) is checked against
+the oracle here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import quadrature as oq
+from oracle import selfconsistent as osc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_14633_gb300 import build
+    build.build()
+    from paper_2407_14633_gb300 import negf
+    return negf.load()
+
+
+def declared_symbols():
+    h = open(os.path.join(ROOT, "include", "negf.h")).read()
+    h = re.sub(r"/\*.*?\*/", "", h, flags=re.S)
+    return sorted(set(re.findall(r"\b(negf_[a-z0-9_]+)\s*\(", h)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_symbols()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_header():
+    from paper_2407_14633_gb300 import negf
+    assert set(negf.exported_symbols()) == set(declared_symbols())
+
+
+def test_status_strings(lib):
+    from paper_2407_14633_gb300 import negf
+    assert lib.negf_strerror(negf.OK) == b"ok"
+    assert b"converge" in lib.negf_strerror(negf.ENOTCONVERGED)
+
+
+@pytest.mark.parametrize("rule", ["gauss", "midpoint"])
+def test_library_grid_matches_oracle_grid(lib, rule):
+    from paper_2407_14633_gb300 import negf
+    r = negf.make_grid(0.0, -0.4, 0.025, 1e-6, -11.0, 2048, 128,
+                       rule=negf.RULE_GAUSS if rule == "gauss" else negf.RULE_MIDPOINT)
+    o = oq.bias_grid(0.0, -0.4, 0.025, 2048, 128, -11.0, 1e-6, rule=rule)
+    for k in ("E", "w", "fS", "fD"):
+        assert np.max(np.abs(r[k] - o[k])) < 1e-13 * max(1.0, np.max(np.abs(o[k])))
+    assert np.max(np.abs(r["z"] - o["z"])) < 1e-13 * np.max(np.abs(o["z"]))
+    assert np.max(np.abs(r["c"] - o["c"])) < 1e-13 * np.max(np.abs(o["c"]))
+
+
+def test_poisson_kappa_matches_oracle(lib):
+    from paper_2407_14633_gb300 import negf
+    assert abs(negf.poisson_kappa() - osc.kappa_from_geometry()) < 1e-12 * osc.kappa_from_geometry()
+
+
+def test_make_grid_rejects_bad_spec(lib):
+    from paper_2407_14633_gb300 import negf
+    with pytest.raises(negf.NegfError):
+        negf.make_grid(0.0, 0.0, 0.025, 1e-6, 5.0, 16, 8)   # E_B above E_min
+
+
+def test_product_path_never_imports_oracle():
+    # the package and the C sources must not reference the oracle
+    pkg = os.path.join(ROOT, "paper_2407_14633_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
