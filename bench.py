@@ -295,6 +295,30 @@ def run_ours(args):
     return 0
 
 
+def run_profile_small(args):
+    """Reduced case of the same kernel for ncu captures: (17,0) real space, N = 128 rings,
+    576 real-axis + 32 contour energies, three NEGF evaluations (no SC loop, no CPU leg)."""
+    import torch
+    from paper_2407_14633_gb300 import negf, synth
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = negf.Context(device=0, stream=stream.cuda_stream)
+    w = synth.realspace_17(N=128, n_real=576, n_cont=32)
+    dev = ctx.device_create(w["N"], block=17, rings_per_block=1, n_chains=1)
+    ctx.build_cnt_realspace(dev, 17, w["t"], w["U_S"], w["U_D"])
+    ctx.set_potential(dev, w["U"])
+    ctx.set_grid_spec(dev, w["mu_S"], w["mu_D"], w["kT"], w["eta"], w["E_B"], w["n_real"], w["n_cont"])
+    ctx.profile(True)
+    for _ in range(3):
+        r = ctx.compute([dev])[0]
+    ms, k = ctx.kernel_time()
+    flops = algorithmic_flops(17, 17, 1.5, w["N"], w["n_real"], w["n_cont"])
+    print(json.dumps({"case": "profile_small", "sweep_ms": ms / k, "tflops": flops / (ms / k * 1e-3) / 1e12,
+                      "I": r["I"]}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,7 +327,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="reduced case of the block sweep for ncu captures")
     args = ap.parse_args()
+    if args.profile_small:
+        return run_profile_small(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
