@@ -284,6 +284,35 @@ int negf_sc_get_state(negf_ctx* ctx, int dev, double* n_in, double* n_in_old, do
 int negf_sc_set_state(negf_ctx* ctx, int dev, const double* n_in, const double* n_in_old,
                       const double* f_old, const double* V, const double* W, int m);
 
+/* ---- evaluation without allocation ------------------------------------------------------ */
+
+/* One NEGF evaluation of a single mode-space chain (1 x 1 blocks) that allocates nothing.
+ * The paper has no counterpart: it exists for callers that cannot allocate device memory
+ * where they run (code building a CUDA graph, allocator-free embedding hosts, tools that
+ * only hand over pre-registered buffers).  The caller owns every input and output; the
+ * library's scratch (work items, per-item ring sums, forward-sweep staging) lives in one
+ * fixed 32 MiB device array that every GPU loading the library reserves until exit.  The
+ * first call on a device looks up that array's address with the device current; make it
+ * before any stream capture.  All calls share the array and it keeps the last call's
+ * contents (what must start at zero is cleared on every call): calls that overlap on the
+ * GPU race on it.  No cudaMalloc, cudaFree or other allocating routine is called.
+ *
+ * stream: cudaStream_t to run on.  Device inputs: Hdiag (n_rings complex, H_{l,l} without
+ * potential), U (n_rings), hsq (n_rings - 1, |H_{l,l+1}|^2), grid E, w, fS, fD (n_real) and
+ * z, c (n_cont complex) as in negf_grid.  Host inputs: lead_S / lead_D = {a1, a2, at, U_lead}
+ * with a1 = |H_{s1,s0}|^2, a2 = |H_{s2,s1}|^2, at = |tau|^2 of the scalar lead (its closed
+ * form, as in negf_set_lead with m = 1).  Device outputs: n (n_rings, required), T (n_real)
+ * and I (1) may be NULL.  Results equal negf_compute's for the same chain.  Returns
+ * NEGF_ENOMEM when ceil(n_real/32) + ceil(n_cont/32) items with n_rings partial sums each,
+ * plus the staging of one 8-warp block (n_rings x 8 KiB), do not fit in the 32 MiB array;
+ * the call is asynchronous on `stream` otherwise. */
+int negf_chain1_compute_noalloc(void* stream, int n_rings, const double* Hdiag, const double* U,
+                                const double* hsq, double g_b, const double* lead_S,
+                                const double* lead_D, int n_real, const double* E,
+                                const double* w, const double* fS, const double* fD, double eta,
+                                int n_cont, const double* z, const double* c, double* n,
+                                double* T, double* I);
+
 /* ---- diagnostics ---------------------------------------------------------------------- */
 
 /* Number of kernel launches the context issued since creation (for accounting). */

@@ -100,6 +100,10 @@ _PROTOS = {
     "negf_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "negf_kernel_time": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_uint64)]),
     "negf_fp64_peak": (C.c_int, [C.c_void_p, _dp]),
+    "negf_chain1_compute_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
+                                              _dp, _dp, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_void_p]),
 }
 
 
