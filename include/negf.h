@@ -66,10 +66,13 @@ typedef struct negf_ctx negf_ctx;
 /* Context options.  stream: a cudaStream_t to run on (e.g. torch.cuda.Stream.cuda_stream),
  * or NULL for a library-owned stream.  hbm_budget_bytes: cap on the library's device
  * memory (0 = no cap); allocations beyond it fail with NEGF_ENOMEM.  precision: one of
- * NEGF_PREC_*.  flag_threshold: mixed precision, the per-energy sum-rule residual above
- * which an energy is recomputed in FP64.  edge_window: mixed precision, energies closer
- * than this (eV) to a lead subband edge are recomputed in FP64.  fault_alloc_after:
- * host-side fault injection for tests, the n-th arena allocation fails (0 = off). */
+ * NEGF_PREC_*.  flag_threshold: mixed precision, the per-energy sum-rule residual (see
+ * negf_out.resid) above which an energy is recomputed in FP64 (0 = default 1e-4).
+ * edge_window: mixed precision, energies closer than this (eV) to a lead subband edge are
+ * recomputed in FP64 (0 = default 0.02).  fault_alloc_after:
+ * host-side fault injection for tests, the n-th arena allocation fails (0 = off).
+ * growth_threshold: mixed precision, energies whose complex64 sweep saw a gL entry larger
+ * than this (1/eV) are recomputed in FP64 (0 = default 20). */
 typedef struct {
   int device_ordinal;
   void* stream;
@@ -78,6 +81,7 @@ typedef struct {
   double flag_threshold;
   double edge_window;
   int fault_alloc_after;
+  double growth_threshold;
 } negf_opts;
 
 /* Create / destroy a context on one GPU.  opts may be NULL (defaults: device 0, own
@@ -189,9 +193,13 @@ int negf_set_grid_spec(negf_ctx* ctx, int dev, const negf_grid_spec* spec);
  * I = g_s (e^2/h) sum_k w_k T(E_k) (fS_k - fD_k).  n_cont / n_real_part (n_rings,
  * optional): the two parts of n.  flags (n_real, optional, int): per-energy precision
  * flags of the mixed path (1 = recomputed in FP64).  resid (n_real, optional): per-energy
- * sum-rule residual of the sweep that produced the result.  Any pointer may be NULL
- * except n.  If on_device != 0 every pointer is device memory on the context's GPU and
- * the results are left there (no host copy). */
+ * sum-rule residual of the complex64 sweep,
+ * max_a |A_S,aa + A_D,aa + 2 Im G_aa| / max_a |2 Im G_aa| over the sites a of the chain
+ * (largest over chains).  growth (n_real, optional): per-energy
+ * largest entry modulus of the left-connected gL_l seen by the complex64 sweep (large
+ * near resonances of the half-open chain, where the backward sweep must cancel it).  Any
+ * pointer may be NULL except n.  If on_device != 0 every pointer is device memory on the
+ * context's GPU and the results are left there (no host copy). */
 typedef struct {
   double* n;
   double* T;
@@ -200,6 +208,7 @@ typedef struct {
   double* n_real_part;
   int* flags;
   double* resid;
+  double* growth;
   int on_device;
 } negf_out;
 
@@ -283,6 +292,43 @@ int negf_sc_get_state(negf_ctx* ctx, int dev, double* n_in, double* n_in_old, do
                       double* V, double* W, int* m);
 int negf_sc_set_state(negf_ctx* ctx, int dev, const double* n_in, const double* n_in_old,
                       const double* f_old, const double* V, const double* W, int m);
+
+/* ---- serving: continuous batching of self-consistent solves ----------------------------- */
+
+/* A request: a mode-space (n_tube,0) nanotube of n_rings rings with n_modes subbands
+ * (1 x 1 blocks, g_b = 2 each), bias point, grid sizes (Gauss-Legendre real axis on the
+ * bias window, contour from E_B), Poisson and Broyden settings.  U0 (n_rings) may be NULL:
+ * the loop then starts from the linear drop between the contacts. */
+typedef struct {
+  int n_rings, n_tube, n_modes;
+  const int* modes;
+  double t, kT, eta, E_B;
+  int n_real, n_cont;
+  negf_bias bias;
+  negf_poisson pois;
+  negf_broyden broyden;
+  const double* U0;
+} negf_request;
+
+/* Queue a request (its arrays are copied); returns a ticket.  Requests are admitted into
+ * device slots in arrival order while their estimated device memory fits the context's
+ * hbm_budget_bytes (one request is always admitted); each scheduler step advances every
+ * admitted request by one self-consistent iteration, all of them in one batched sweep
+ * launch, and retires the finished ones.  A request's result is bitwise the same alone and
+ * in any mix. */
+int negf_submit(negf_ctx* ctx, const negf_request* req, uint64_t* ticket);
+/* Run one scheduler step; *active receives the number of requests on the GPU. */
+int negf_serve_step(negf_ctx* ctx, int* active);
+/* NEGF_EBUSY while the request is queued or running; then fills res (n, U: n_rings; T:
+ * n_real; history: iterations) and returns its status (NEGF_OK or NEGF_ENOTCONVERGED). */
+int negf_poll(negf_ctx* ctx, uint64_t ticket, negf_sc_result* res);
+/* Drive the scheduler until the request finished or timeout_ms passed (NEGF_ETIMEDOUT). */
+int negf_wait(negf_ctx* ctx, uint64_t ticket, int timeout_ms, negf_sc_result* res);
+/* Cancel a queued or running request; its slot is freed at the next step. */
+int negf_cancel(negf_ctx* ctx, uint64_t ticket);
+/* Host wall-clock times (s, steady clock) of submission, admission and completion. */
+int negf_request_times(negf_ctx* ctx, uint64_t ticket, double* t_submit, double* t_start,
+                       double* t_done);
 
 /* ---- evaluation without allocation ------------------------------------------------------ */
 

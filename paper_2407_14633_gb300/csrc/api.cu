@@ -5,6 +5,7 @@
 #include <complex>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "ctx.h"
 
@@ -84,7 +85,8 @@ Dev* get_dev(Ctx* c, int dev) {
 
 void free_dev(Ctx* c, Dev* d) {
   for (auto& ch : d->ch) {
-    for (DBuf* b : {&ch.dHdiag, &ch.dHup, &ch.dcs_cnt, &ch.dcs_idx, &ch.dcs_val, &ch.dhsq})
+    for (DBuf* b : {&ch.dHdiag, &ch.dHup, &ch.dcs_cnt, &ch.dcs_idx, &ch.dcs_val, &ch.drs_cnt, &ch.drs_idx,
+                    &ch.drs_val, &ch.dhsq})
       c->arena.release(*b);
     for (int s = 0; s < 2; ++s)
       for (DBuf* b : {&ch.da1[s], &ch.da2[s], &ch.dat[s], &ch.dsites[s], &ch.dtw[s]})
@@ -115,6 +117,8 @@ int upload_lead(Ctx* c, ChainData& ch, int side) {
   circulant_moduli(L.T1, L.m, a1);
   circulant_moduli(L.T2, L.m, a2);
   circulant_moduli(L.tau, L.m, at);
+  L.a1 = a1;
+  L.a2 = a2;
   for (int k = 0; k < L.m; ++k) {
     const double ang = 2.0 * M_PI * k / L.m;
     tw[2 * k] = std::cos(ang);
@@ -167,6 +171,52 @@ int upload_chain(Ctx* c, Dev* d, ChainData& ch) {
   if ((rc = upload(c, ch.dcs_cnt, cnt.data(), cnt.size() * 4))) return rc;
   if ((rc = upload(c, ch.dcs_idx, idx.data(), idx.size() * 4))) return rc;
   if ((rc = upload(c, ch.dcs_val, val.data(), val.size() * 8))) return rc;
+  // row-sparse form (row r: entries (column, value)), padded to the same kmax
+  int rkmax = 1;
+  for (int l = 0; l < L - 1; ++l)
+    for (int r = 0; r < b; ++r) {
+      int n = 0;
+      for (int col = 0; col < b; ++col) {
+        const double* v = &ch.Hup[2 * ((size_t)l * b * b + (size_t)r * b + col)];
+        if (v[0] != 0.0 || v[1] != 0.0) ++n;
+      }
+      rkmax = std::max(rkmax, n);
+    }
+  const int km = std::max(kmax, rkmax);
+  if (km != kmax) {
+    // re-pad the column form to the common width
+    std::vector<int> idx2((size_t)nl * b * km, 0);
+    std::vector<double> val2((size_t)nl * b * km * 2, 0.0);
+    for (size_t q = 0; q < (size_t)nl * b; ++q)
+      for (int e = 0; e < kmax; ++e) {
+        idx2[q * km + e] = idx[q * kmax + e];
+        val2[2 * (q * km + e)] = val[2 * (q * kmax + e)];
+        val2[2 * (q * km + e) + 1] = val[2 * (q * kmax + e) + 1];
+      }
+    if ((rc = upload(c, ch.dcs_idx, idx2.data(), idx2.size() * 4))) return rc;
+    if ((rc = upload(c, ch.dcs_val, val2.data(), val2.size() * 8))) return rc;
+    ch.kmax = km;
+  }
+  std::vector<int> rcnt((size_t)nl * b, 0), ridx((size_t)nl * b * km, 0);
+  std::vector<double> rval((size_t)nl * b * km * 2, 0.0);
+  for (int l = 0; l < L - 1; ++l)
+    for (int r = 0; r < b; ++r) {
+      int n = 0;
+      for (int col = 0; col < b; ++col) {
+        const double* v = &ch.Hup[2 * ((size_t)l * b * b + (size_t)r * b + col)];
+        if (v[0] != 0.0 || v[1] != 0.0) {
+          const size_t e = ((size_t)l * b + r) * km + n;
+          ridx[e] = col;
+          rval[2 * e] = v[0];
+          rval[2 * e + 1] = v[1];
+          ++n;
+        }
+      }
+      rcnt[(size_t)l * b + r] = n;
+    }
+  if ((rc = upload(c, ch.drs_cnt, rcnt.data(), rcnt.size() * 4))) return rc;
+  if ((rc = upload(c, ch.drs_idx, ridx.data(), ridx.size() * 4))) return rc;
+  if ((rc = upload(c, ch.drs_val, rval.data(), rval.size() * 8))) return rc;
   std::vector<double> hsq(nl, 0.0);
   if (b == 1)
     for (int l = 0; l < L - 1; ++l) hsq[l] = ch.Hup[2 * l] * ch.Hup[2 * l] + ch.Hup[2 * l + 1] * ch.Hup[2 * l + 1];
@@ -203,39 +253,62 @@ std::vector<double> dagger_row(const std::vector<double>& row, int n) {
 }
 
 // ---- quadrature on the host (grids are set-up data, uploaded once per bias point)
-// Gauss-Legendre by Newton iteration on P_n with the three-term recurrence
-void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
-  x.assign(n, 0.0);
-  w.assign(n, 0.0);
-  for (int i = 0; i < n; ++i) {
-    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
-    double dp = 1.0;
-    for (int it = 0; it < 100; ++it) {
-      double p0 = 1.0, p1 = z;
-      for (int j = 1; j < n; ++j) {
-        const double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
-        p0 = p1;
-        p1 = p2;
-      }
-      if (n == 1) {
-        p0 = 1.0;
-        p1 = z;
-      }
-      dp = n * (z * p1 - p0) / (z * z - 1.0);
-      const double dz = p1 / dp;
-      z -= dz;
-      if (std::fabs(dz) < 1e-16) break;
-    }
+// Gauss-Legendre by Newton iteration on P_n with the three-term recurrence.  The rule is
+// symmetric (x_{n-1-k} = -x_k), so only the upper half of the nodes is iterated; large
+// rules spread the nodes over host threads (each node is independent).
+void gl_node(int n, int i, double& x_out, double& w_out) {
+  double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+  for (int it = 0; it < 100; ++it) {
     double p0 = 1.0, p1 = z;
     for (int j = 1; j < n; ++j) {
       const double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
       p0 = p1;
       p1 = p2;
     }
-    dp = n * (z * p1 - p0) / (z * z - 1.0);
-    x[n - 1 - i] = z;
-    w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    const double dp = n * (z * p1 - p0) / (z * z - 1.0);
+    const double dz = p1 / dp;
+    z -= dz;
+    if (std::fabs(dz) < 1e-16) break;
   }
+  double p0 = 1.0, p1 = z;
+  for (int j = 1; j < n; ++j) {
+    const double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+    p0 = p1;
+    p1 = p2;
+  }
+  const double dp = n * (z * p1 - p0) / (z * z - 1.0);
+  x_out = z;
+  w_out = 2.0 / ((1.0 - z * z) * dp * dp);
+}
+
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const int half = (n + 1) / 2;   // nodes i = 0..half-1 are the non-negative ones
+  auto work = [&](int i0, int i1) {
+    for (int i = i0; i < i1; ++i) {
+      double z, wz;
+      gl_node(n, i, z, wz);
+      x[n - 1 - i] = z;
+      w[n - 1 - i] = wz;
+      x[i] = -z;
+      w[i] = wz;
+    }
+  };
+  unsigned nt = std::thread::hardware_concurrency();
+  if (n < 512 || nt < 2) {
+    work(0, half);
+  } else {
+    nt = std::min<unsigned>(nt, 32);
+    std::vector<std::thread> th;
+    const int chunk = (half + (int)nt - 1) / (int)nt;
+    for (unsigned t = 0; t < nt; ++t) {
+      const int i0 = (int)t * chunk, i1 = std::min(half, i0 + chunk);
+      if (i0 < i1) th.emplace_back(work, i0, i1);
+    }
+    for (auto& t : th) t.join();
+  }
+  if (n % 2) x[n / 2] = 0.0;   // the middle node of an odd rule is exactly 0
 }
 
 }  // namespace
@@ -304,6 +377,7 @@ int negf_create(negf_ctx** out, const negf_opts* opts) {
   }
   if (c->opts.flag_threshold <= 0.0) c->opts.flag_threshold = 1e-4;
   if (c->opts.edge_window <= 0.0) c->opts.edge_window = 0.02;
+  if (c->opts.growth_threshold <= 0.0) c->opts.growth_threshold = 20.0;
   c->ordinal = c->opts.device_ordinal;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -571,6 +645,7 @@ int negf_set_grid(negf_ctx* c, int dev, const negf_grid* g) {
   d->n_real = g->n_real;
   d->n_cont = g->n_cont;
   d->eta = g->eta;
+  d->hE.assign(g->E, g->E + g->n_real);
   d->grid_set = true;
   d->spec_set = false;
   return NEGF_OK;

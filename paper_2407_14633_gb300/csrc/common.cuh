@@ -141,6 +141,7 @@ struct SweepArgs {
   double* partial;        // per-item per-ring partial sums
   double* Tpart;          // per-chain T(E)
   double* resid;          // per-lane sum-rule residual (may be null)
+  double* growth;         // per-lane max |gL entry| over the forward sweep (may be null)
   unsigned char* stage;   // staging of the forward sweep, per resident warp
   long long stage_stride; // bytes per resident warp
   int* status;            // device error flag (0 ok)
@@ -152,12 +153,18 @@ int launch_sweep_b1_f64(const SweepArgs& a, int grid, int block, cudaStream_t s)
 int launch_sweep_b1_f32(const SweepArgs& a, int grid, int block, cudaStream_t s);
 // thread-per-lane sweep of 2x2 blocks
 int launch_sweep_b2_f64(const SweepArgs& a, int grid, int block, cudaStream_t s);
+int launch_sweep_b2_f32(const SweepArgs& a, int grid, int block, cudaStream_t s);
 // warp-per-lane sweep of b x b blocks (b <= MAX_BLOCK) with smem matrices
 int launch_sweep_blk_f64(const SweepArgs& a, int b_max, int m_max, int grid, int warps,
                          cudaStream_t s);
 __host__ __device__ size_t sweep_blk_smem_bytes(int b, int m, int warps);
+__host__ __device__ size_t sweep_blk_smem_bytes_t(int b, int m, int esize);
+__host__ __device__ size_t sweep_blk_smem_bytes_nm(int b, int m, int esize, int nm);
+int launch_sweep_blk_t(bool fp32, const SweepArgs& a, int b_max, int m_max, int grid, int warps, cudaStream_t s);
+int sweep_blk_occupancy_t(bool fp32, int warps, size_t smem);
 // resident CTAs per SM of a sweep kernel (sets the dynamic shared memory limit first)
 int sweep_chain_occupancy(int cls, int threads, size_t smem);
+int sweep_chain_occupancy_t(bool fp32, int cls, int threads, size_t smem);
 int sweep_blk_occupancy(int warps, size_t smem);
 
 struct ReduceDev {

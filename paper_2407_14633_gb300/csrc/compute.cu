@@ -69,6 +69,9 @@ DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
     cv.cs_cnt = (const int*)ch.dcs_cnt.p;
     cv.cs_idx = (const int*)ch.dcs_idx.p;
     cv.cs_val = (const cd*)ch.dcs_val.p;
+    cv.rs_cnt = (const int*)ch.drs_cnt.p;
+    cv.rs_idx = (const int*)ch.drs_idx.p;
+    cv.rs_val = (const cd*)ch.drs_val.p;
     cv.kmax = ch.kmax;
     cv.hsq = (const double*)ch.dhsq.p;
     cv.g_b = ch.g_b;
@@ -100,9 +103,24 @@ int check_ready(Ctx* c, Dev* d) {
 // context scratch.  launch_plan then issues only stream-ordered device work (counter
 // reset, sweeps, second stage), so it can be captured in a CUDA graph and replayed.
 void free_plan_bufs(Ctx* c, PlanBufs& b) {
-  for (DBuf* x : {&b.views, &b.items, &b.order, &b.counter, &b.partial, &b.tpart, &b.stage, &b.reduce, &b.status})
+  for (DBuf* x : {&b.views, &b.items, &b.order, &b.counter, &b.partial, &b.tpart, &b.stage, &b.reduce, &b.status,
+                  &b.resid, &b.order2, &b.growth})
     c->arena.release(*x);
 }
+
+// CTA width of the wide-block kernel: enough threads for the b x b products
+static int blk_warps_for(int b) { return b <= 20 ? 1 : (b <= 28 ? 2 : 4); }
+
+static bool item_f32(int kind, int prec) {
+  return prec == NEGF_PREC_FP32 || (prec == NEGF_PREC_MIXED && kind == 0);
+}
+// group of an item: 0 (1x1), 1 (2x2), 2/3/4 (wide blocks, 1/2/4 warps), + 5 for FP32
+static int group_of(int cls, int b, bool f32) {
+  int g = cls < 2 ? cls : 2 + (blk_warps_for(b) == 1 ? 0 : (blk_warps_for(b) == 2 ? 1 : 2));
+  return g + (f32 ? 5 : 0);
+}
+static int group_class(int g) { return std::min(g % 5, 2); }
+static bool group_f32(int g) { return g >= 5; }
 
 int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOverride>* ov, int chain_only,
                Plan& P, PlanBufs* bufs) {
@@ -111,23 +129,36 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
   P = Plan();
   P.bufs = bufs ? bufs : &c->scratch;
   PlanBufs& B = *P.bufs;
+  P.prec = c->opts.precision;
   P.devs = devs;
   P.views.resize(nd);
   std::vector<WorkItem>& items = P.items;
   P.it0.assign(nd + 1, 0);
   long long part = 0, tpos = 0;
-  std::vector<long long> tbase(nd);
-  int Lmax[3] = {0, 0, 0}, bmax = 1, mmax = 1;
+  std::vector<long long>& tbase = P.tbase;
+  tbase.assign(nd, 0);
+  int Lmax[5] = {0, 0, 0, 0, 0};
+  for (int g = 0; g < NGROUPS; ++g) {
+    P.gb[g] = 1;
+    P.gm[g] = 1;
+    P.gw[g] = 1;
+  }
   for (int di = 0; di < nd; ++di) {
     Dev* d = devs[di];
     const ViewOverride* o = ov ? &(*ov)[di] : nullptr;
     P.views[di] = make_view(c, d, o);
     const DeviceView& v = P.views[di];
     const int cls = kernel_class(d);
-    Lmax[cls] = std::max(Lmax[cls], d->L);
+    const int g0 = group_of(cls, d->block, false);
+    Lmax[g0] = std::max(Lmax[g0], d->L);
     if (cls == 2) {
-      bmax = std::max(bmax, d->block);
-      for (auto& ch : d->ch) mmax = std::max(mmax, std::max(ch.lead[0].m, ch.lead[1].m));
+      int mm = 1;
+      for (auto& ch : d->ch) mm = std::max(mm, std::max(ch.lead[0].m, ch.lead[1].m));
+      for (int f = 0; f < 2; ++f) {
+        P.gb[g0 + 5 * f] = std::max(P.gb[g0 + 5 * f], d->block);
+        P.gm[g0 + 5 * f] = std::max(P.gm[g0 + 5 * f], mm);
+        P.gw[g0 + 5 * f] = blk_warps_for(d->block);
+      }
     }
     const int chunk = (cls == 2 || (o && o->one_energy_per_item)) ? 1 : LANES;
     P.it0[di] = (int)items.size();
@@ -143,7 +174,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
           W.kind = kind;
           W.e0 = e0;
           W.ne = std::min(chunk, ne - e0);
-          W.pad = cls;
+          W.pad = group_of(cls, d->block, item_f32(kind, c->opts.precision));
           W.part = part;
           W.tout = tpos + (long long)ch * v.n_real + e0;
           part += d->n_rings;
@@ -158,58 +189,141 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
   if (n_items == 0) return set_err(c, NEGF_EINVAL, "nothing to compute");
   P.n_items = n_items;
   P.tpos = tpos;
-  P.bmax = bmax;
-  P.mmax = mmax;
 
-  // schedule order per kernel class: longest first
-  std::vector<int> order[3];
+  // band-edge flags of the mixed path: |E - U_lead - e| < window for an edge e of a lead
+  // mode, e in {+-|sqrt(a1) - sqrt(a2)|, +-(sqrt(a1) + sqrt(a2))}
+  if (P.prec == NEGF_PREC_MIXED) {
+    P.edge_flag.assign(tpos, 0);
+    const double win = c->opts.edge_window;
+    for (int di = 0; di < nd; ++di) {
+      Dev* d = devs[di];
+      const DeviceView& v = P.views[di];
+      if (!(ov && (*ov)[di].n_real >= 0)) {
+        for (int ch = 0; ch < d->n_chains; ++ch) {
+          for (int k = 0; k < v.n_real && k < (int)d->hE.size(); ++k) {
+            bool near = false;
+            for (int side = 0; side < 2 && !near; ++side) {
+              const HostLead& Ld = d->ch[ch].lead[side];
+              const double Ul = (ov && (*ov)[di].zero_lead_U) ? 0.0 : Ld.U;
+              for (size_t j = 0; j < Ld.a1.size() && !near; ++j) {
+                const double p = std::sqrt(Ld.a1[j]), q = std::sqrt(Ld.a2[j]);
+                const double e[4] = {std::fabs(p - q), -std::fabs(p - q), p + q, -(p + q)};
+                for (int t = 0; t < 4; ++t)
+                  if (std::fabs(d->hE[k] - Ul - e[t]) < win) near = true;
+              }
+            }
+            P.edge_flag[tbase[di] + (long long)ch * v.n_real + k] = near;
+          }
+        }
+      }
+    }
+  }
+
+  // schedule order per group: longest first
+  std::vector<int> order[NGROUPS];
   for (int i = 0; i < n_items; ++i) order[items[i].pad].push_back(i);
-  for (int cls = 0; cls < 3; ++cls) {
+  for (int g = 0; g < NGROUPS; ++g) {
     auto cost = [&](int i) {
       const Dev* d = devs[items[i].dev];
       return (double)d->L * (items[i].kind == 0 ? 2.0 : 1.0) * (double)d->block * d->block * d->block;
     };
-    std::stable_sort(order[cls].begin(), order[cls].end(), [&](int a, int b) { return cost(a) > cost(b); });
+    std::stable_sort(order[g].begin(), order[g].end(), [&](int a, int b) { return cost(a) > cost(b); });
   }
   std::vector<int> order_all;
-  for (int cls = 0; cls < 3; ++cls) {
-    P.ooff[cls] = (int)order_all.size();
-    P.ncls[cls] = (int)order[cls].size();
-    order_all.insert(order_all.end(), order[cls].begin(), order[cls].end());
+  for (int g = 0; g < NGROUPS; ++g) {
+    P.ooff[g] = (int)order_all.size();
+    P.ncls[g] = (int)order[g].size();
+    order_all.insert(order_all.end(), order[g].begin(), order[g].end());
   }
 
-  // launch geometry and staging
+  // launch geometry and staging per group (staging sized for FP64 elements)
   const Tune tune;
   P.block_threads = tune.block_threads;
-  P.blk_warps = tune.blk_warps;
-  size_t smem[3];
-  smem[0] = smem[1] = (size_t)(tune.block_threads / 32) * 32 * 33 * sizeof(double);
-  smem[2] = sweep_blk_smem_bytes(bmax, mmax, tune.blk_warps);
-  P.stride[0] = (long long)Lmax[0] * 4 * 32 * 8;
-  P.stride[1] = (long long)Lmax[1] * 12 * 32 * 8;
-  P.stride[2] = (long long)Lmax[2] * (bmax * bmax + bmax * mmax) * 16;
-  for (int cls = 0; cls < 3; ++cls) P.grid[cls] = 0;
-  if (P.ncls[0]) P.grid[0] = c->sms * sweep_chain_occupancy(0, tune.block_threads, smem[0]);
-  if (P.ncls[1]) P.grid[1] = c->sms * sweep_chain_occupancy(1, tune.block_threads, smem[1]);
-  if (P.ncls[2]) {
-    if (smem[2] > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
-    P.grid[2] = c->sms * sweep_blk_occupancy(tune.blk_warps, smem[2]);
-  }
+  const size_t csmem = (size_t)(tune.block_threads / 32) * 32 * 33 * sizeof(double);
   long long stage_bytes = 0;
-  for (int cls = 0; cls < 3; ++cls) {
-    if (!P.ncls[cls]) continue;
-    const int wpb = cls == 2 ? tune.blk_warps : tune.block_threads / 32;
-    const int need_blocks = (P.ncls[cls] + wpb - 1) / wpb;
-    P.grid[cls] = std::max(1, std::min(P.grid[cls], need_blocks));
-    stage_bytes = std::max(stage_bytes, P.stride[cls] * P.grid[cls] * wpb);
+  for (int g = 0; g < NGROUPS; ++g) {
+    const int cls = group_class(g);
+    const int L = Lmax[g % 5];
+    if (cls == 0) P.stride[g] = (long long)L * 5 * 32 * 8;
+    else if (cls == 1) P.stride[g] = (long long)L * 12 * 32 * 8;
+    else P.stride[g] = (long long)L * (P.gb[g] * P.gb[g] + P.gb[g] * P.gm[g]) * 16;
+    P.grid[g] = 0;
+    if (!P.ncls[g]) continue;
+    const bool f32 = group_f32(g);
+    int per_sm, wpb;
+    if (cls < 2) {
+      per_sm = sweep_chain_occupancy_t(f32, cls, tune.block_threads, csmem);
+      wpb = tune.block_threads / 32;
+    } else {
+      const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16);
+      if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
+      per_sm = sweep_blk_occupancy_t(f32, P.gw[g], sm);
+      wpb = 1;   // one lane (item) per CTA
+    }
+    const int need = cls < 2 ? (P.ncls[g] + wpb - 1) / wpb : P.ncls[g];
+    P.grid[g] = std::max(1, std::min(c->sms * per_sm, need));
+    stage_bytes = std::max(stage_bytes, P.stride[g] * P.grid[g] * wpb);
   }
+  // the MIXED recompute runs flagged FP32 items of group g + 5 through FP64 group g,
+  // with the FP32 group's grid and the FP64 group's staging stride and shared memory
+  if (P.prec == NEGF_PREC_MIXED)
+    for (int g = 0; g < 5; ++g) {
+      if (!P.ncls[g + 5]) continue;
+      const int cls = group_class(g);
+      const int wpb = cls < 2 ? tune.block_threads / 32 : 1;
+      stage_bytes = std::max(stage_bytes, P.stride[g] * (long long)P.grid[g + 5] * wpb);
+      if (cls == 2) {
+        const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], 16);
+        if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
+        sweep_blk_occupancy_t(false, P.gw[g], sm);
+      } else {
+        sweep_chain_occupancy_t(false, cls, tune.block_threads, csmem);
+      }
+    }
 
+  // Under an HBM budget the staging of the forward sweep (per resident warp / CTA) is what
+  // adapts: resident CTAs are capped so that it fits beside everything else.
+  if (c->arena.budget) {
+    // a buffer that has to grow is released before its replacement is allocated
+    auto extra = [](const DBuf& b, size_t need) -> long long {
+      return need > b.bytes ? (long long)(need - b.bytes) : 0;
+    };
+    long long other = extra(B.views, sizeof(DeviceView) * nd) + extra(B.items, sizeof(WorkItem) * n_items) +
+                      extra(B.order, sizeof(int) * n_items) + extra(B.partial, sizeof(double) * std::max<long long>(part, 1)) +
+                      extra(B.tpart, sizeof(double) * std::max<long long>(tpos, 1)) + extra(B.reduce, sizeof(ReduceDev) * nd) +
+                      extra(B.counter, sizeof(int) * 16) + extra(B.status, sizeof(int));
+    if (P.prec != NEGF_PREC_FP64)
+      other += extra(B.resid, sizeof(double) * tpos) + extra(B.growth, sizeof(double) * tpos) + extra(B.order2, sizeof(int) * n_items);
+    for (int di = 0; di < nd; ++di) {
+      Dev* d = devs[di];
+      const size_t nr8 = (size_t)d->n_rings * 8;
+      other += extra(d->dT, sizeof(double) * std::max(P.views[di].n_real, 1)) + extra(d->dn, nr8) +
+               extra(d->dnr, nr8) + extra(d->dnc, nr8) + extra(d->dI, 8) + extra(d->dgb, 64);
+    }
+    const long long cap = (long long)c->arena.budget - (long long)c->arena.used + (long long)B.stage.bytes - other;
+    if (stage_bytes > cap) {
+      stage_bytes = 0;
+      for (int g = 0; g < NGROUPS; ++g) {
+        if (!P.ncls[g]) continue;
+        const int wpb = group_class(g) < 2 ? tune.block_threads / 32 : 1;
+        // an FP32 group's grid also runs its FP64 recompute, with the FP64 stride
+        const long long per = std::max(P.stride[g], P.stride[g % 5]) * wpb;
+        const long long fit = per > 0 ? cap / per : 1;
+        if (fit < 1) return set_err(c, NEGF_ENOMEM, "budget too small for one resident block of the sweep");
+        P.grid[g] = (int)std::min<long long>(P.grid[g], fit);
+        stage_bytes = std::max(stage_bytes, per * P.grid[g]);
+      }
+    }
+  }
   if (!ensure(c, B.views, sizeof(DeviceView) * nd) || !ensure(c, B.items, sizeof(WorkItem) * n_items) ||
-      !ensure(c, B.order, sizeof(int) * n_items) || !ensure(c, B.counter, sizeof(int) * 4) ||
+      !ensure(c, B.order, sizeof(int) * n_items) || !ensure(c, B.counter, sizeof(int) * 16) ||
       !ensure(c, B.partial, sizeof(double) * std::max<long long>(part, 1)) ||
       !ensure(c, B.tpart, sizeof(double) * std::max<long long>(tpos, 1)) ||
       !ensure(c, B.stage, (size_t)std::max<long long>(stage_bytes, 16)) ||
-      !ensure(c, B.reduce, sizeof(ReduceDev) * nd) || !ensure(c, B.status, sizeof(int)))
+      !ensure(c, B.reduce, sizeof(ReduceDev) * nd) || !ensure(c, B.status, sizeof(int)) ||
+      (P.prec != NEGF_PREC_FP64 && (!ensure(c, B.resid, sizeof(double) * std::max<long long>(tpos, 1)) ||
+                                    !ensure(c, B.growth, sizeof(double) * std::max<long long>(tpos, 1)) ||
+                                    !ensure(c, B.order2, sizeof(int) * n_items))))
     return NEGF_ENOMEM;
   std::vector<ReduceDev> rd(nd);
   for (int di = 0; di < nd; ++di) {
@@ -253,10 +367,92 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
   return NEGF_OK;
 }
 
-int launch_plan(Ctx* c, const Plan& P) {
+static int launch_group(Ctx* c, const Plan& P, int g, const int* order, int n, int grid, double* resid,
+                        double* growth) {
+  const PlanBufs& B = *P.bufs;
+  const int cls = group_class(g);
+  const bool f32 = group_f32(g);
+  SweepArgs a;
+  a.devs = (const DeviceView*)B.views.p;
+  a.items = (const WorkItem*)B.items.p;
+  a.order = order;
+  a.n_items = n;
+  a.counter = (int*)B.counter.p + g;
+  a.partial = (double*)B.partial.p;
+  a.Tpart = (double*)B.tpart.p;
+  a.resid = resid;
+  a.growth = growth;
+  a.stage = (unsigned char*)B.stage.p;
+  a.stage_stride = P.stride[g % 5];
+  a.status = (int*)B.status.p;
+  cudaStream_t s = c->stream;
+  int rc;
+  if (cls == 0)
+    rc = f32 ? launch_sweep_b1_f32(a, grid, P.block_threads, s) : launch_sweep_b1_f64(a, grid, P.block_threads, s);
+  else if (cls == 1)
+    rc = f32 ? launch_sweep_b2_f32(a, grid, P.block_threads, s) : launch_sweep_b2_f64(a, grid, P.block_threads, s);
+  else
+    rc = launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], grid, P.gw[g], s);
+  if (rc) return set_err(c, NEGF_ECUDA, "sweep launch failed");
+  ++c->launches;
+  return NEGF_OK;
+}
+
+// MIXED: read the FP32 residuals, flag real-axis lanes (sum-rule residual above the
+// threshold, or a lead band edge within the window) and re-run the items holding them in
+// FP64 into the same partial and T slots.
+static int mixed_recompute(Ctx* c, Plan& P) {
+  const PlanBufs& B = *P.bufs;
+  cudaStream_t s = c->stream;
+  P.resid.assign(P.tpos, 0.0);
+  P.growth.assign(P.tpos, 0.0);
+  if (cudaMemcpyAsync(P.resid.data(), B.resid.p, sizeof(double) * P.tpos, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(P.growth.data(), B.growth.p, sizeof(double) * P.tpos, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return set_err(c, NEGF_ECUDA, "mixed-precision sweep failed");
+  const double thr = c->opts.flag_threshold;
+  const double gthr = c->opts.growth_threshold > 0.0 ? c->opts.growth_threshold : 20.0;
+  P.flags.assign(P.tpos, 0);
+  std::vector<int> redo[5];
+  for (int i = 0; i < P.n_items; ++i) {
+    const WorkItem& W = P.items[i];
+    if (W.kind != 0 || W.pad < 5) continue;
+    bool any = false;
+    for (int e = 0; e < W.ne; ++e) {
+      const long long t = W.tout + e;
+      if (!(P.resid[t] <= thr) || !(P.growth[t] <= gthr) || (!P.edge_flag.empty() && P.edge_flag[t])) any = true;
+    }
+    if (any) {
+      redo[W.pad - 5].push_back(i);
+      for (int e = 0; e < W.ne; ++e) P.flags[W.tout + e] = 1;
+    }
+  }
+  std::vector<int> all;
+  int off[5];
+  for (int g = 0; g < 5; ++g) {
+    off[g] = (int)all.size();
+    all.insert(all.end(), redo[g].begin(), redo[g].end());
+  }
+  P.recomputed = (int)all.size();
+  if (all.empty()) return NEGF_OK;
+  if (cudaMemcpy(B.order2.p, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemsetAsync(B.counter.p, 0, sizeof(int) * 16, s) != cudaSuccess)
+    return set_err(c, NEGF_ECUDA, "recompute upload failed");
+  for (int g = 0; g < 5; ++g) {
+    if (redo[g].empty()) continue;
+    const int cls = group_class(g);
+    const int n = (int)redo[g].size();
+    const int grid = std::max(1, std::min(P.grid[g + 5], cls < 2 ? (n + 7) / 8 : n));
+    int rc = launch_group(c, P, g, (const int*)B.order2.p + off[g], n, grid, nullptr, nullptr);
+    if (rc) return rc;
+  }
+  return NEGF_OK;
+}
+
+int launch_plan(Ctx* c, Plan& P) {
   cudaStream_t s = c->stream;
   const PlanBufs& B = *P.bufs;
-  if (cudaMemsetAsync(B.counter.p, 0, sizeof(int) * 4, s) != cudaSuccess ||
+  if (cudaMemsetAsync(B.counter.p, 0, sizeof(int) * 16, s) != cudaSuccess ||
       cudaMemsetAsync(B.tpart.p, 0, sizeof(double) * std::max<long long>(P.tpos, 1), s) != cudaSuccess)
     return set_err(c, NEGF_ECUDA, "counter reset failed");
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -268,29 +464,24 @@ int launch_plan(Ctx* c, const Plan& P) {
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
   }
-  for (int cls = 0; cls < 3; ++cls) {
-    if (!P.ncls[cls]) continue;
-    SweepArgs a;
-    a.devs = (const DeviceView*)B.views.p;
-    a.items = (const WorkItem*)B.items.p;
-    a.order = (const int*)B.order.p + P.ooff[cls];
-    a.n_items = P.ncls[cls];
-    a.counter = (int*)B.counter.p + cls;
-    a.partial = (double*)B.partial.p;
-    a.Tpart = (double*)B.tpart.p;
-    a.resid = nullptr;
-    a.stage = (unsigned char*)B.stage.p;
-    a.stage_stride = P.stride[cls];
-    a.status = (int*)B.status.p;
-    int rc;
-    if (cls == 0)
-      rc = launch_sweep_b1_f64(a, P.grid[0], P.block_threads, s);
-    else if (cls == 1)
-      rc = launch_sweep_b2_f64(a, P.grid[1], P.block_threads, s);
-    else
-      rc = launch_sweep_blk_f64(a, P.bmax, P.mmax, P.grid[2], P.blk_warps, s);
-    if (rc) return set_err(c, NEGF_ECUDA, "sweep launch failed");
-    ++c->launches;
+  for (int g = 0; g < NGROUPS; ++g) {
+    if (!P.ncls[g]) continue;
+    double* resid = group_f32(g) ? (double*)B.resid.p : nullptr;
+    double* growth = group_f32(g) ? (double*)B.growth.p : nullptr;
+    int rc = launch_group(c, P, g, (const int*)B.order.p + P.ooff[g], P.ncls[g], P.grid[g], resid, growth);
+    if (rc) return rc;
+  }
+  if (P.prec == NEGF_PREC_MIXED) {
+    if (cap != cudaStreamCaptureStatusNone) return set_err(c, NEGF_EINVAL, "mixed precision cannot be captured");
+    int rc = mixed_recompute(c, P);
+    if (rc) return rc;
+  } else if (P.prec == NEGF_PREC_FP32 && cap == cudaStreamCaptureStatusNone && P.want_diag) {
+    P.resid.assign(P.tpos, 0.0);
+    P.growth.assign(P.tpos, 0.0);
+    if (cudaMemcpyAsync(P.resid.data(), B.resid.p, sizeof(double) * P.tpos, cudaMemcpyDeviceToHost, s) ||
+        cudaMemcpyAsync(P.growth.data(), B.growth.p, sizeof(double) * P.tpos, cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s))
+      return set_err(c, NEGF_ECUDA, "diagnostics read failed");
   }
   if (timed) {
     cudaEventRecord(e1, s);
@@ -314,12 +505,24 @@ int copy_out(Ctx* c, const Plan& P, const negf_out* outs) {
     if (o.n_cont && cudaMemcpyAsync(o.n_cont, d->dnc.p, d->n_rings * 8, k, s)) return set_err(c, NEGF_ECUDA, "copy out failed");
     if (o.T && nr > 0 && cudaMemcpyAsync(o.T, d->dT.p, (size_t)nr * 8, k, s)) return set_err(c, NEGF_ECUDA, "copy out failed");
     if (o.I && cudaMemcpyAsync(o.I, d->dI.p, 8, k, s)) return set_err(c, NEGF_ECUDA, "copy out failed");
-    if (o.flags && nr > 0) {
-      if (o.on_device) {
-        if (cudaMemsetAsync(o.flags, 0, (size_t)nr * 4, s)) return set_err(c, NEGF_ECUDA, "copy out failed");
-      } else {
-        memset(o.flags, 0, (size_t)nr * 4);
-      }
+    // per-energy flags / residuals / growth over the chains (host summaries of the precision path)
+    if ((o.flags || o.resid || o.growth) && nr > 0) {
+      std::vector<int> fl(nr, 0);
+      std::vector<double> rs(nr, 0.0), gr(nr, 0.0);
+      for (int ch = 0; ch < d->n_chains; ++ch)
+        for (int e = 0; e < nr; ++e) {
+          const long long t = P.tbase[di] + (long long)ch * nr + e;
+          if (!P.flags.empty()) fl[e] |= P.flags[t];
+          if (!P.resid.empty()) rs[e] = std::max(rs[e], P.resid[t]);
+          if (!P.growth.empty()) gr[e] = std::max(gr[e], P.growth[t]);
+        }
+      if (o.growth && cudaMemcpyAsync(o.growth, gr.data(), (size_t)nr * 8, o.on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s))
+        return set_err(c, NEGF_ECUDA, "copy out failed");
+      if (o.flags && cudaMemcpyAsync(o.flags, fl.data(), (size_t)nr * 4, o.on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s))
+        return set_err(c, NEGF_ECUDA, "copy out failed");
+      if (o.resid && cudaMemcpyAsync(o.resid, rs.data(), (size_t)nr * 8, o.on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s))
+        return set_err(c, NEGF_ECUDA, "copy out failed");
+      if (cudaStreamSynchronize(s) != cudaSuccess) return set_err(c, NEGF_ECUDA, "copy out failed");
     }
   }
   return NEGF_OK;
@@ -331,6 +534,9 @@ static int run_batch(Ctx* c, const std::vector<Dev*>& devs, const std::vector<Vi
   Plan P;
   int rc = build_plan(c, devs, ov, chain_only, P);
   if (rc) return rc;
+  if (outs)
+    for (size_t i = 0; i < devs.size(); ++i)
+      if (outs[i].resid || outs[i].growth) P.want_diag = true;
   if ((rc = launch_plan(c, P))) return rc;
   if (outs && (rc = copy_out(c, P, outs))) return rc;
   if (items_out) *items_out = P.items;

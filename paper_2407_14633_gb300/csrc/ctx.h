@@ -32,6 +32,7 @@ struct Arena {
 struct HostLead {
   int m = 0;
   double U = 0.0;
+  std::vector<double> a1, a2;   // per-mode |lambda_j(T1)|^2, |lambda_j(T2)|^2 (band edges)
   std::vector<double> T1, T2, tau;  // first rows, 2m each
   std::vector<int> sites;
   bool set = false;
@@ -43,7 +44,7 @@ struct ChainData {
   bool h_set = false;
   HostLead lead[2];
   // device copies
-  DBuf dHdiag, dHup, dcs_cnt, dcs_idx, dcs_val, dhsq;
+  DBuf dHdiag, dHup, dcs_cnt, dcs_idx, dcs_val, drs_cnt, drs_idx, drs_val, dhsq;
   DBuf da1[2], da2[2], dat[2], dsites[2], dtw[2];
   int kmax = 0;
 };
@@ -52,7 +53,7 @@ struct ChainData {
 // self-consistent session owns its own, so its captured graph never sees a buffer that a
 // later call reallocated.
 struct PlanBufs {
-  DBuf views, items, order, counter, partial, tpart, stage, reduce, status;
+  DBuf views, items, order, counter, partial, tpart, stage, reduce, status, resid, order2, growth;
 };
 
 struct ScSession;
@@ -65,6 +66,7 @@ struct Dev {
   // grid (host copies) and spec
   int n_real = 0, n_cont = 0;
   double eta = 0.0;
+  std::vector<double> hE;        // host copy of the real-axis nodes
   bool grid_set = false;
   bool spec_set = false;
   negf_grid_spec spec{};
@@ -115,22 +117,37 @@ struct ViewOverride {
   const cd *z = nullptr, *c = nullptr;
   bool one_energy_per_item = false;
 };
+// Items are launched in groups: kernel class (1x1, 2x2, wide blocks by CTA width 1/2/4
+// warps) x element type (FP64, FP32), ten groups.  The CTA width of a wide-block item follows
+// from its own block size, so a device's arithmetic never depends on its batch.  MIXED runs
+// real-axis lanes in FP32 and contour lanes in FP64, then re-runs flagged real-axis items in
+// FP64 into the same partial slots.
+constexpr int NGROUPS = 10;
 struct Plan {
   PlanBufs* bufs = nullptr;
   std::vector<Dev*> devs;
   std::vector<DeviceView> views;
   std::vector<WorkItem> items;
   std::vector<int> it0;
-  int n_items = 0, bmax = 1, mmax = 1, block_threads = 256, blk_warps = 1;
-  int grid[3] = {0, 0, 0}, ooff[3] = {0, 0, 0}, ncls[3] = {0, 0, 0};
-  long long stride[3] = {0, 0, 0};
+  std::vector<long long> tbase;
+  int prec = NEGF_PREC_FP64;
+  int n_items = 0, block_threads = 256;
+  int grid[NGROUPS] = {0}, ooff[NGROUPS] = {0}, ncls[NGROUPS] = {0};
+  int gb[NGROUPS] = {0}, gm[NGROUPS] = {0}, gw[NGROUPS] = {0};   // bmax, mmax, warps of wide-block groups
+  long long stride[NGROUPS] = {0};
   long long tpos = 0;
+  std::vector<unsigned char> edge_flag;   // per real energy of each device (tbase order, chain 0)
+  std::vector<int> flags;                 // per T slot after the MIXED recompute
+  std::vector<double> resid;              // per T slot
+  std::vector<double> growth;             // per T slot
+  int recomputed = 0;
+  bool want_diag = false;
 };
 int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOverride>* ov, int chain_only,
                Plan& P, PlanBufs* bufs = nullptr);
 void free_plan_bufs(Ctx* c, PlanBufs& b);
 void sc_session_free(Ctx* c, Dev* d);
-int launch_plan(Ctx* c, const Plan& P);
+int launch_plan(Ctx* c, Plan& P);
 int copy_out(Ctx* c, const Plan& P, const negf_out* outs);
 int check_ready(Ctx* c, Dev* d);
 Dev* find_device(Ctx* c, int dev);
@@ -141,3 +158,8 @@ DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o);
 }  // namespace negf
 
 struct negf_ctx : public negf::Ctx {};
+
+namespace negf {
+// every Ctx is created as a negf_ctx (negf_create); internal code calling the public API
+inline negf_ctx* pub(Ctx* c) { return static_cast<negf_ctx*>(c); }
+}  // namespace negf

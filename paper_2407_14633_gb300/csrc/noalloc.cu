@@ -206,6 +206,7 @@ extern "C" int negf_chain1_compute_noalloc(void* stream, int n_rings, const doub
   a.partial = reinterpret_cast<double*>(base + lo.partial);
   a.Tpart = reinterpret_cast<double*>(base + lo.tpart);
   a.resid = nullptr;
+  a.growth = nullptr;
   a.stage = base + lo.stage;
   a.stage_stride = (long long)n_rings * 4 * 32 * sizeof(double);
   a.status = reinterpret_cast<int*>(base + lo.counter) + 3;

@@ -141,7 +141,8 @@ int negf_sc_begin(negf_ctx* c, int dev, const negf_bias* bias, const negf_poisso
   if (cudaMemcpy(s->sc.p, &sd, sizeof(sd), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(set_err(c, NEGF_ECUDA, "upload failed"));
   if (cudaMallocHost(&s->h_state, sizeof(int)) != cudaSuccess) return fail(set_err(c, NEGF_ENOMEM, "pinned alloc failed"));
-  s->kernels_per_iter = 2 + (s->plan.ncls[0] > 0) + (s->plan.ncls[1] > 0) + (s->plan.ncls[2] > 0) + 1;
+  s->kernels_per_iter = 3;
+  for (int g = 0; g < NGROUPS; ++g) s->kernels_per_iter += (s->plan.ncls[g] > 0);
   // capture one iteration (falls back to direct launches if the stream cannot be captured)
   const ScDev* dsc = (const ScDev*)s->sc.p;
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {

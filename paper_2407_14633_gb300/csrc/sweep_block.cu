@@ -1,19 +1,28 @@
-// Warp-per-lane recursive Green's function sweep for wide ring blocks (real space).
+// Recursive Green's function sweep for wide ring blocks (real space): one CTA of NW warps
+// owns one (device, chain, energy) lane and keeps its b x b complex blocks in shared
+// memory; every product spreads its outputs over the CTA's threads.
 //
-// One warp owns one (device, chain, energy) lane and keeps its b x b complex blocks in
-// shared memory; every product spreads its outputs over the 32 threads.  The algorithm
-// is the left-connected recursion (Alg. 2 reading) with the lead columns propagated as
-// factors of the broadening matrices:  Gamma_l = L_l L_l^dagger with
-// L_l = F diag(sqrt(gamma_j)) from the circulant lead (F the ring Fourier basis), so that
+// The algorithm is the left-connected recursion (Alg. 2 reading) with the lead columns
+// propagated as factors of the broadening matrices, Gamma_l = L_l L_l^dagger with
+// L_l = F diag(sqrt(gamma_j)) from the circulant lead (F the ring Fourier basis):
 //   forward   X = H_{l,l-1} gL_{l-1},  gL_l = (alpha_l - X H_{l-1,l})^{-1},
 //             R_l = X R_{l-1} (R_0 = L_S)                 [R_l = G_{l,l}^{-1} G_{l,0} L_S]
 //   backward  Z = gL_l H_{l,l+1},  G_ll = gL_l + Z G_{l+1,l+1} (H_{l+1,l} gL_l),
 //             K_l = Z K_{l+1} (K_{L-1} = G_{L-1,L-1} L_D)  [K_l = G_{l,L-1} L_D]
 //   A_S,ll = (G_ll R_l)(G_ll R_l)^dagger,  A_D,ll = K_l K_l^dagger,
 //   T = || L_S^dagger K_0 ||_F^2 = Tr[Gamma_S G_{0,L-1} Gamma_D G_{0,L-1}^dagger].
-// Products with the coupling blocks use their padded sparse form (kmax entries per row or
-// column; kmax = b for dense couplings).  gL_l and R_l are staged per resident warp in
-// global memory.  FP64 throughout; the FP64 pipe is the bound on GB300.
+// Products with the coupling blocks use their column-sparse form (kmax entries per
+// column; kmax = b for dense couplings).  gL_l and R_l are staged per resident CTA in
+// global memory.
+//
+// Element type T: double (the FP64 path; on GB300 the FP64 pipe is the bound) or float
+// (the complex64 sweep of the mixed-precision path; lead self-energies are still formed
+// in FP64 and the quadrature weights applied in FP64).  For real-axis lanes the kernel
+// can also record the lane's residual of the sum rule
+//   -2 Im G_aa = A_S,aa + A_D,aa + 2 eta (G G^dagger)_aa,
+// max_a |A_S,aa + A_D,aa + 2 Im G_aa| / max_a |2 Im G_aa| (the eta term is below rounding
+// except at states the leads do not reach), which the mixed path uses to decide which
+// energies to recompute in FP64.
 #include "common.cuh"
 #include "lead.cuh"
 
@@ -21,66 +30,103 @@ namespace negf {
 
 namespace {
 
-__device__ __forceinline__ cd czero() { return mk(0.0, 0.0); }
+template <int NW>
+__device__ __forceinline__ void csync() {
+  if (NW == 1)
+    __syncwarp();
+  else
+    __syncthreads();
+}
 
-// C (R x N, ldc) = [Add +] A (R x K, lda) * B (K x N, ldb); outputs spread over the warp
-__device__ __forceinline__ void wgemm(cd* C, int ldc, const cd* A, int lda, const cd* B, int ldb,
-                                      int R, int K, int N, const cd* Add, int ldadd, int lane) {
+template <typename T>
+__device__ __forceinline__ cx<T> cz() {
+  return mk(T(0), T(0));
+}
+template <typename T>
+__device__ __forceinline__ cx<T> tc(cd v) {
+  return mk((T)v.re, (T)v.im);
+}
+
+// C (R x N, ldc) = [Add +] A (R x K, lda) * B (K x N, ldb); two outputs per thread and two
+// partial sums per output keep eight independent FMA chains in flight
+template <typename T, int NT>
+__device__ __forceinline__ void bgemm(cx<T>* C, int ldc, const cx<T>* A, int lda, const cx<T>* B, int ldb,
+                                      int R, int K, int N, const cx<T>* Add, int ldadd, int tid) {
   const int tot = R * N;
-  for (int o = lane; o < tot; o += 32) {
-    const int r = o / N, c = o - r * N;
-    cd acc = Add ? Add[r * ldadd + c] : czero();
-    const cd* a = A + r * lda;
-    const cd* b = B + c;
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) acc = cmac(acc, a[k], b[k * ldb]);
-    C[r * ldc + c] = acc;
+  for (int o0 = tid; o0 < tot; o0 += 2 * NT) {
+    const int o1 = o0 + NT;
+    const bool two = o1 < tot;
+    const int r0 = o0 / N, c0 = o0 - r0 * N;
+    const int r1 = two ? o1 / N : r0, c1 = two ? o1 - r1 * N : c0;
+    const cx<T>* a0 = A + r0 * lda;
+    const cx<T>* a1 = A + r1 * lda;
+    const cx<T>* b0 = B + c0;
+    const cx<T>* b1 = B + c1;
+    cx<T> s00 = cz<T>(), s01 = cz<T>(), s10 = cz<T>(), s11 = cz<T>();
+    int k = 0;
+    for (; k + 1 < K; k += 2) {
+      s00 = cmac(s00, a0[k], b0[k * ldb]);
+      s10 = cmac(s10, a1[k], b1[k * ldb]);
+      s01 = cmac(s01, a0[k + 1], b0[(k + 1) * ldb]);
+      s11 = cmac(s11, a1[k + 1], b1[(k + 1) * ldb]);
+    }
+    if (k < K) {
+      s00 = cmac(s00, a0[k], b0[k * ldb]);
+      s10 = cmac(s10, a1[k], b1[k * ldb]);
+    }
+    cx<T> v0 = s00 + s01, v1 = s10 + s11;
+    if (Add) {
+      v0 = v0 + Add[r0 * ldadd + c0];
+      v1 = v1 + Add[r1 * ldadd + c1];
+    }
+    C[r0 * ldc + c0] = v0;
+    if (two) C[r1 * ldc + c1] = v1;
   }
 }
 
-// C (b x N) = H_{l+1,l} * M  where H_{l+1,l} = Hup_l^dagger: row r uses column r of Hup_l
-__device__ __forceinline__ void hdn_times(cd* C, const cd* M, int ldm, int N, int b,
-                                          const int* cs_cnt, const int* cs_idx,
-                                          const cd* cs_val, int kmax, int lane) {
+// C (b x N) = H_{l+1,l} M where H_{l+1,l} = Hup_l^dagger: row r uses column r of Hup_l
+template <typename T, int NT>
+__device__ __forceinline__ void hdn_times(cx<T>* C, const cx<T>* M, int ldm, int N, int b, const int* cnt,
+                                          const int* idx, const cd* val, int kmax, int tid) {
   const int tot = b * N;
-  for (int o = lane; o < tot; o += 32) {
+  for (int o = tid; o < tot; o += NT) {
     const int r = o / N, c = o - r * N;
-    cd acc = czero();
-    const int n = cs_cnt[r];
-    for (int e = 0; e < n; ++e) {
-      const int k = cs_idx[r * kmax + e];
-      acc = cmac_cj(acc, cs_val[r * kmax + e], M[k * ldm + c]);
-    }
+    cx<T> acc = cz<T>();
+    const int n = cnt[r];
+    for (int e = 0; e < n; ++e) acc = cmac_cj(acc, tc<T>(val[r * kmax + e]), M[idx[r * kmax + e] * ldm + c]);
     C[r * N + c] = acc;
   }
 }
 
-// C (R x b) = M (R x b) * Hup_l : column c uses column c of Hup_l
-__device__ __forceinline__ void times_hup(cd* C, const cd* M, int R, int b, const int* cs_cnt,
-                                          const int* cs_idx, const cd* cs_val, int kmax,
-                                          int lane) {
+// C (R x b) = M (R x b) Hup_l: column c uses column c of Hup_l
+template <typename T, int NT>
+__device__ __forceinline__ void times_hup(cx<T>* C, const cx<T>* M, int R, int b, const int* cnt, const int* idx,
+                                          const cd* val, int kmax, int tid) {
   const int tot = R * b;
-  for (int o = lane; o < tot; o += 32) {
+  for (int o = tid; o < tot; o += NT) {
     const int r = o / b, c = o - r * b;
-    cd acc = czero();
-    const int n = cs_cnt[c];
-    for (int e = 0; e < n; ++e) {
-      const int k = cs_idx[c * kmax + e];
-      acc = cmac(acc, M[r * b + k], cs_val[c * kmax + e]);
-    }
+    cx<T> acc = cz<T>();
+    const int n = cnt[c];
+    for (int e = 0; e < n; ++e) acc = cmac(acc, M[r * b + idx[c * kmax + e]], tc<T>(val[c * kmax + e]));
     C[r * b + c] = acc;
   }
 }
 
-// in-place Gauss-Jordan inverse of the b x b block A with partial pivoting (row swaps
-// recorded in perm, undone on the columns at the end); col: b scratch entries
-__device__ void winv(cd* A, int b, cd* col, int* perm, int lane) {
+// In-place Gauss-Jordan inverse of the b x b block A with partial pivoting (row swaps
+// recorded in perm, undone on the columns at the end).  Pivot step k: save column k
+// (f_i = A[i][k]); scale row k by 1/A[k][k] with A[k][k] := 1/A[k][k]; zero column k
+// elsewhere; then one uniform update A[i][j] -= f_i A[k][j] for every i != k and every j
+// (for j = k it yields -f_i / A[k][k]): four fused multiply-adds per element.
+template <typename T, int NW>
+__device__ void binv(cx<T>* A, int b, cx<T>* col, int* perm, float* rbest, int* ridx, int tid) {
+  constexpr int NT = 32 * NW;
+  const int lane = tid & 31, wid = tid >> 5;
   for (int k = 0; k < b; ++k) {
-    // pivot search on column k, rows k..b-1
-    double best = -1.0;
+    float best = -1.0f;
     int bi = k;
-    for (int i = k + lane; i < b; i += 32) {
-      const double m = abs2(A[i * b + k]);
+    for (int i = k + tid; i < b; i += NT) {
+      const cx<T> v = A[i * b + k];
+      const float m = fmaf((float)v.re, (float)v.re, (float)v.im * (float)v.im);
       if (m > best) {
         best = m;
         bi = i;
@@ -88,97 +134,220 @@ __device__ void winv(cd* A, int b, cd* col, int* perm, int lane) {
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
       const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
       if (ob > best || (ob == best && oi < bi)) {
         best = ob;
         bi = oi;
       }
     }
-    if (lane == 0) perm[k] = bi;
+    if (NW > 1) {
+      if (lane == 0) {
+        rbest[wid] = best;
+        ridx[wid] = bi;
+      }
+      __syncthreads();
+      best = rbest[0];
+      bi = ridx[0];
+      for (int w = 1; w < NW; ++w)
+        if (rbest[w] > best || (rbest[w] == best && ridx[w] < bi)) {
+          best = rbest[w];
+          bi = ridx[w];
+        }
+    }
+    if (tid == 0) perm[k] = bi;
     if (bi != k) {
-      for (int j = lane; j < b; j += 32) {
-        const cd t = A[k * b + j];
+      csync<NW>();
+      for (int j = tid; j < b; j += NT) {
+        const cx<T> t = A[k * b + j];
         A[k * b + j] = A[bi * b + j];
         A[bi * b + j] = t;
       }
     }
-    __syncwarp();
-    const cd ip = crecip(A[k * b + k]);
-    for (int i = lane; i < b; i += 32) col[i] = A[i * b + k];
-    __syncwarp();
-    for (int j = lane; j < b; j += 32) A[k * b + j] = (j == k) ? ip : A[k * b + j] * ip;
-    __syncwarp();
+    csync<NW>();
+    const cx<T> ip = crecip(A[k * b + k]);
+    for (int i = tid; i < b; i += NT) col[i] = A[i * b + k];
+    csync<NW>();
+    for (int j = tid; j < b; j += NT) A[k * b + j] = (j == k) ? ip : A[k * b + j] * ip;
+    for (int i = tid; i < b; i += NT)
+      if (i != k) A[i * b + k] = cz<T>();
+    csync<NW>();
+    // three independent elements per thread and pass: loads, then updates, then stores
     const int tot = (b - 1) * b;
-    for (int o = lane; o < tot; o += 32) {
-      int i = o / b;
-      const int j = o - i * b;
-      i += (i >= k);
-      const cd f = col[i];
-      if (j == k) {
-        A[i * b + k] = czero() - f * ip;
-      } else {
-        A[i * b + j] = A[i * b + j] - f * A[k * b + j];
+    for (int o0 = tid; o0 < tot; o0 += 3 * NT) {
+      int q[3];
+      cx<T> x[3], f[3], r[3];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const int o = o0 + u * NT;
+        const int oo = o < tot ? o : o0;
+        int i = oo / b;
+        const int j = oo - i * b;
+        i += (i >= k);
+        q[u] = o < tot ? i * b + j : -1;
+        x[u] = A[i * b + j];
+        f[u] = col[i];
+        r[u] = A[k * b + j];
       }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) x[u] = cmac(x[u], cz<T>() - f[u], r[u]);
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+        if (q[u] >= 0) A[q[u]] = x[u];
     }
-    __syncwarp();
+    csync<NW>();
   }
-  __syncwarp();
   for (int k = b - 1; k >= 0; --k) {
     const int p = perm[k];
     if (p != k) {
-      for (int i = lane; i < b; i += 32) {
-        const cd t = A[i * b + k];
+      for (int i = tid; i < b; i += NT) {
+        const cx<T> t = A[i * b + k];
         A[i * b + k] = A[i * b + p];
         A[i * b + p] = t;
       }
     }
-    __syncwarp();
+    csync<NW>();
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+// deterministic CTA sum / max (warp butterfly, then the warps in order)
+template <int NW>
+__device__ __forceinline__ double bsum(double v, double* red, int tid) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return v;
+  if (NW == 1) return v;
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < NW; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+template <int NW>
+__device__ __forceinline__ double cta_max(double v, double* red, int tid) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+  if (NW == 1) return v;
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = red[0];
+  for (int w = 1; w < NW; ++w) s = fmax(s, red[w]);
+  __syncthreads();
+  return s;
 }
 
 }  // namespace
 
-__host__ __device__ size_t sweep_blk_smem_bytes(int b, int m, int warps) {
-  // per warp: 4 b^2 + 3 b m complex, 2 m sigma/gamma rows, b scratch column, b ints
-  size_t per = (size_t)(4 * b * b + 3 * b * m + 4 * m + b) * sizeof(cd) + (size_t)b * sizeof(int);
-  per = (per + 15) & ~(size_t)15;
-  return per * warps;
+// row-sparse products for the two-sided variant:
+// C (b x N) = H_{l,l+1} M: row r uses row r of Hup_l
+template <typename T, int NT>
+__device__ __forceinline__ void hup_times(cx<T>* C, const cx<T>* M, int ldm, int N, int b, const int* cnt,
+                                          const int* idx, const cd* val, int kmax, int tid) {
+  const int tot = b * N;
+  for (int o = tid; o < tot; o += NT) {
+    const int r = o / N, c = o - r * N;
+    cx<T> acc = cz<T>();
+    const int n = cnt[r];
+    for (int e = 0; e < n; ++e) acc = cmac(acc, tc<T>(val[r * kmax + e]), M[idx[r * kmax + e] * ldm + c]);
+    C[r * N + c] = acc;
+  }
+}
+// C (R x b) = M H_{l+1,l} = M Hup_l^dagger: column c uses row c of Hup_l, conjugated
+template <typename T, int NT>
+__device__ __forceinline__ void times_hdn(cx<T>* C, const cx<T>* M, int R, int b, const int* cnt, const int* idx,
+                                          const cd* val, int kmax, int tid) {
+  const int tot = R * b;
+  for (int o = tid; o < tot; o += NT) {
+    const int r = o / b, c = o - r * b;
+    cx<T> acc = cz<T>();
+    const int n = cnt[c];
+    for (int e = 0; e < n; ++e) acc = cmac_cj(acc, tc<T>(val[c * kmax + e]), M[r * b + idx[c * kmax + e]]);
+    C[r * b + c] = acc;
+  }
 }
 
-__global__ void __launch_bounds__(256) sweep_blk_kernel(SweepArgs a, int bmax, int mmax) {
+// shared memory of one CTA: NM b^2 + 3 b m + b elements of size esize (NM = 4, or 6 for the
+// two-sided variant), FP64 lead rows (2 m complex + 2 m real), b pivot ints, reductions
+__host__ __device__ size_t sweep_blk_smem_bytes_nm(int b, int m, int esize, int nm) {
+  size_t per = (size_t)(nm * b * b + 3 * b * m + b) * esize;
+  per = (per + 15) & ~(size_t)15;
+  per += (size_t)2 * m * 16 + (size_t)2 * m * 8 + (size_t)(b + 1) * 4 + 8 * 8 + 8 * 4 + 8 * 4;
+  return (per + 15) & ~(size_t)15;
+}
+// FP32 sweeps use the two-sided backward (six b x b buffers), FP64 the Dyson update (four)
+__host__ __device__ size_t sweep_blk_smem_bytes_t(int b, int m, int esize) {
+  return sweep_blk_smem_bytes_nm(b, m, esize, esize == 8 ? 6 : 4);
+}
+__host__ __device__ size_t sweep_blk_smem_bytes(int b, int m, int warps) {
+  (void)warps;
+  return sweep_blk_smem_bytes_t(b, m, 16);
+}
+
+// alpha_l - Sub (Sub may be null): eps I - H_ll - U_ring - Sigma_S (l = 0) - Sigma_D (l = L-1),
+// assembled in FP64 and rounded to T
+template <typename T, int NW>
+__device__ __forceinline__ void alpha_minus(cx<T>* out, const cx<T>* Sub, int l, int L, int b, int rpb, int spr,
+                                            cd eps, const DeviceView& D, const ChainView& C, const cd* sigS,
+                                            const cd* sigD, int tid) {
+  constexpr int NT = 32 * NW;
+  const cd* hd = C.Hdiag + (long long)l * b * b;
+  const int nn = b * b;
+  for (int o = tid; o < nn; o += NT) {
+    const int r = o / b, c = o - r * b;
+    cd v = mk(-hd[o].re, -hd[o].im);
+    if (r == c) v = v + mk(eps.re - D.U[l * rpb + r / spr], eps.im);
+    out[o] = Sub ? tc<T>(v) - Sub[o] : tc<T>(v);
+  }
+  csync<NW>();
+  for (int side = 0; side < 2; ++side) {
+    if ((side == 0 && l != 0) || (side == 1 && l != L - 1)) continue;
+    const LeadView& Lv = C.lead[side];
+    const cd* row = side ? sigD : sigS;
+    const int m = Lv.m;
+    for (int o = tid; o < m * m; o += NT) {
+      const int s = o / m, t = o - s * m;
+      const int q = Lv.sites[s] * b + Lv.sites[t];
+      out[q] = out[q] - tc<T>(row[((s - t) % m + m) % m]);
+    }
+    csync<NW>();
+  }
+}
+
+template <typename T, int NW, bool TWO>
+__global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bmax, int mmax) {
+  constexpr int NT = 32 * NW;
+  constexpr int NM = TWO ? 6 : 4;
   extern __shared__ __align__(16) unsigned char sm_blk[];
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-  const size_t per = sweep_blk_smem_bytes(bmax, mmax, 1);
-  cd* base = reinterpret_cast<cd*>(sm_blk + per * wib);
+  const int tid = threadIdx.x;
   const int bb = bmax * bmax, bm = bmax * mmax;
-  cd* M0 = base;             // b x b
-  cd* M1 = M0 + bb;          // b x b
-  cd* M2 = M1 + bb;          // b x b
-  cd* M3 = M2 + bb;          // b x b
-  cd* V0 = M3 + bb;          // b x m
-  cd* V1 = V0 + bm;          // b x m
-  cd* V2 = V1 + bm;          // b x m
-  cd* sigS = V2 + bm;        // m: circulant first row of Sigma_S / per-mode sqrt(gamma) in .re
+  cx<T>* M0 = reinterpret_cast<cx<T>*>(sm_blk);
+  cx<T>* M1 = M0 + bb;
+  cx<T>* M2 = M1 + bb;
+  cx<T>* M3 = M2 + bb;
+  cx<T>* M4 = M3 + bb;   // two-sided only
+  cx<T>* M5 = M4 + bb;   // two-sided only
+  cx<T>* V0 = M0 + NM * bb;
+  cx<T>* V1 = V0 + bm;
+  cx<T>* V2 = V1 + bm;
+  cx<T>* col = V2 + bm;
+  size_t off = (size_t)(NM * bb + 3 * bm + bmax) * sizeof(cx<T>);
+  off = (off + 15) & ~(size_t)15;
+  cd* sigS = reinterpret_cast<cd*>(sm_blk + off);
   cd* sigD = sigS + mmax;
-  cd* sqS = sigD + mmax;     // m: sqrt(gamma_j / m) of the source (re)
-  cd* sqD = sqS + mmax;
-  cd* col = sqD + mmax;      // b
-  int* perm = reinterpret_cast<int*>(col + bmax);
-  unsigned char* stage = a.stage + (long long)gw * a.stage_stride;
+  double* sqS = reinterpret_cast<double*>(sigD + mmax);
+  double* sqD = sqS + mmax;
+  double* redd = sqD + mmax;
+  float* redf = reinterpret_cast<float*>(redd + 8);
+  int* redi = reinterpret_cast<int*>(redf + 8);
+  int* perm = redi + 8;
+  __shared__ int s_item;
+  unsigned char* stage = a.stage + (long long)blockIdx.x * a.stage_stride;
 
   for (;;) {
-    int it = 0;
-    if (lane == 0) it = atomicAdd(a.counter, 1);
-    it = __shfl_sync(0xffffffffu, it, 0);
+    if (tid == 0) s_item = atomicAdd(a.counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
     if (it >= a.n_items) break;
     const WorkItem W = a.items[a.order[it]];
     const DeviceView& D = a.devs[W.dev];
@@ -197,7 +366,7 @@ __global__ void __launch_bounds__(256) sweep_blk_kernel(SweepArgs a, int bmax, i
 
     cd eps;
     double wS = 0.0, wD = 0.0;
-    cd kap = czero();
+    cd kap = mk(0.0, 0.0);
     if (real) {
       eps = mk(D.E[k], D.eta);
       wS = g * D.w[k] * D.fS[k] * (0.5 / 3.14159265358979323846);
@@ -207,104 +376,77 @@ __global__ void __launch_bounds__(256) sweep_blk_kernel(SweepArgs a, int bmax, i
       kap = scale(D.c[k], g / 3.14159265358979323846);
     }
 
-    // ---- lead self-energies: per-mode roots (FP64), circulant first rows
-    //      Sigma[s][t] = (1/m) sum_j sigma_j w^{j (s - t)}, stored as row[d], d = (s - t) mod m
+    // ---- lead self-energies in FP64: per-mode roots sigma_j, then the circulant first
+    //      row Sigma[s][t] = (1/m) sum_j sigma_j w^{j (s - t)}, kept as row[d], d = (s - t) mod m
+    //      (a thread holds at most two modes: m <= MAX_LEAD <= 2 * NT)
     for (int side = 0; side < 2; ++side) {
       const LeadView& Lv = C.lead[side];
       cd* row = side ? sigD : sigS;
-      cd* sq = side ? sqD : sqS;
+      double* sq = side ? sqD : sqS;
       const int m = Lv.m;
-      // per-mode sigma_j into `col` scratch (m <= MAX_LEAD, col has b >= m entries)
-      for (int j = lane; j < m; j += 32) {
+      for (int j = tid; j < m; j += NT) {
         const cd sj = mode_sigma(Lv, j, eps);
-        col[j] = sj;
-        sq[j] = mk(sqrt(fmax(-2.0 * sj.im, 0.0) / m), 0.0);
+        row[j] = sj;
+        sq[j] = sqrt(fmax(-2.0 * sj.im, 0.0) / m);
       }
-      __syncwarp();
-      for (int d = lane; d < m; d += 32) {
-        cd acc = czero();
+      csync<NW>();
+      cd keep[2] = {mk(0.0, 0.0), mk(0.0, 0.0)};
+      for (int d = tid, q = 0; d < m && q < 2; d += NT, ++q) {
+        cd acc = mk(0.0, 0.0);
         for (int j = 0; j < m; ++j) {
           const int e = (j * d) % m;
-          acc = cmac(acc, col[j], mk(Lv.tw[2 * e], Lv.tw[2 * e + 1]));
+          acc = cmac(acc, row[j], mk(Lv.tw[2 * e], Lv.tw[2 * e + 1]));
         }
-        row[d] = scale(acc, 1.0 / m);
+        keep[q] = scale(acc, 1.0 / m);
       }
-      __syncwarp();
+      csync<NW>();
+      for (int d = tid, q = 0; d < m && q < 2; d += NT, ++q) row[d] = keep[q];
+      csync<NW>();
     }
 
     // ---- forward sweep: P = gL_{l-1} (M0), A (M1), X (M2); R (V0), Rn (V1)
-    cd* P = M0;
-    cd* A = M1;
-    cd* X = M2;
-    cd* R = V0;
-    cd* Rn = V1;
-    const long long lstride = (long long)(bb + (real ? bm : 0)) * sizeof(cd);
+    cx<T>* P = M0;
+    cx<T>* A = M1;
+    cx<T>* X = M2;
+    cx<T>* R = V0;
+    cx<T>* Rn = V1;
+    const long long lstride = (long long)(bb + (real ? bm : 0)) * sizeof(cx<T>);
+    float gmax = 0.0f;   // largest |gL_l entry|^2 of this thread (growth diagnostic)
     for (int l = 0; l < L; ++l) {
-      const cd* hd = C.Hdiag + (long long)l * b * b;
       if (l > 0) {
         const int* ccnt = C.cs_cnt + (long long)(l - 1) * b;
         const int* cidx = C.cs_idx + (long long)(l - 1) * b * kmax;
         const cd* cval = C.cs_val + (long long)(l - 1) * b * kmax;
-        // X = H_{l,l-1} gL_{l-1}
-        hdn_times(X, P, b, b, b, ccnt, cidx, cval, kmax, lane);
-        __syncwarp();
-        // A = X H_{l-1,l}  (subtracted below)
-        times_hup(A, X, b, b, ccnt, cidx, cval, kmax, lane);
-        if (real) {
-          __syncwarp();
-          wgemm(Rn, mS, X, b, R, mS, b, b, mS, nullptr, 0, lane);
-        }
+        hdn_times<T, NT>(X, P, b, b, b, ccnt, cidx, cval, kmax, tid);            // X = H_{l,l-1} gL_{l-1}
+        csync<NW>();
+        times_hup<T, NT>(A, X, b, b, ccnt, cidx, cval, kmax, tid);               // y_l = X H_{l-1,l}
+        if (real) bgemm<T, NT>(Rn, mS, X, b, R, mS, b, b, mS, nullptr, 0, tid);  // R_l = X R_{l-1}
+        csync<NW>();
+        alpha_minus<T, NW>(A, A, l, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);  // alpha_l - y_l
       } else {
-        for (int o = lane; o < nn; o += 32) A[o] = czero();
         if (real) {
           // R_0 = L_S: rows at the lead sites, L_S[site_s][j] = w^{j s} sqrt(gamma_j / m)
-          for (int o = lane; o < b * mS; o += 32) Rn[o] = czero();
-          __syncwarp();
-          for (int o = lane; o < mS * mS; o += 32) {
+          for (int o = tid; o < b * mS; o += NT) Rn[o] = cz<T>();
+          csync<NW>();
+          for (int o = tid; o < mS * mS; o += NT) {
             const int s = o / mS, j = o - s * mS;
             const int e = (j * s) % mS;
-            Rn[LS.sites[s] * mS + j] = scale(mk(LS.tw[2 * e], LS.tw[2 * e + 1]), sqS[j].re);
+            Rn[LS.sites[s] * mS + j] = tc<T>(scale(mk(LS.tw[2 * e], LS.tw[2 * e + 1]), sqS[j]));
           }
         }
+        alpha_minus<T, NW>(A, nullptr, 0, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);
       }
-      __syncwarp();
-      // A = eps I - H_ll - U - X H_{l-1,l} - Sigma
-      for (int o = lane; o < nn; o += 32) {
-        const int r = o / b, c = o - r * b;
-        cd v = czero() - hd[o] - A[o];
-        if (r == c) {
-          const int ring = l * rpb + r / spr;
-          v = v + mk(eps.re - D.U[ring], eps.im);
-        }
-        A[o] = v;
-      }
-      __syncwarp();
-      if (l == 0) {
-        for (int o = lane; o < mS * mS; o += 32) {
-          const int s = o / mS, t = o - s * mS;
-          const int d = ((s - t) % mS + mS) % mS;
-          const int rs = LS.sites[s], rt = LS.sites[t];
-          A[rs * b + rt] = A[rs * b + rt] - sigS[d];
-        }
-        __syncwarp();
-      }
-      if (l == L - 1) {
-        for (int o = lane; o < mD * mD; o += 32) {
-          const int s = o / mD, t = o - s * mD;
-          const int d = ((s - t) % mD + mD) % mD;
-          const int rs = LD.sites[s], rt = LD.sites[t];
-          A[rs * b + rt] = A[rs * b + rt] - sigD[d];
-        }
-        __syncwarp();
-      }
-      winv(A, b, col, perm, lane);
+      binv<T, NW>(A, b, col, perm, redf, redi, tid);
       // stage gL_l (and R_l)
-      cd* sg = reinterpret_cast<cd*>(stage + (long long)l * lstride);
-      for (int o = lane; o < nn; o += 32) sg[o] = A[o];
+      cx<T>* sg = reinterpret_cast<cx<T>*>(stage + (long long)l * lstride);
+      for (int o = tid; o < nn; o += NT) {
+        sg[o] = A[o];
+        if (a.growth) gmax = fmaxf(gmax, fmaf((float)A[o].re, (float)A[o].re, (float)A[o].im * (float)A[o].im));
+      }
       if (real)
-        for (int o = lane; o < b * mS; o += 32) sg[bb + o] = Rn[o];
-      __syncwarp();
-      cd* t = P;
+        for (int o = tid; o < b * mS; o += NT) sg[bb + o] = Rn[o];
+      csync<NW>();
+      cx<T>* t = P;
       P = A;
       A = t;
       t = R;
@@ -312,119 +454,213 @@ __global__ void __launch_bounds__(256) sweep_blk_kernel(SweepArgs a, int bmax, i
       Rn = t;
     }
 
-    // ---- backward sweep.  G (P: gL_{L-1} = G_{L-1,L-1}), Gl, Z, Wm; K, Kn, Rl
-    cd* G = P;
-    cd* Gl = A;
-    cd* Z = X;
-    cd* Wm = M3;   // the forward used M0..M2 only
-    cd* K = (R == V0) ? V1 : V0;   // R holds R_{L-1}; use the other two for K
-    cd* Kn = V2;
-    cd* Rl = R;
+    // ---- backward sweep
+    //  Dyson variant:     G (P: gL_{L-1} = G_{L-1,L-1}), Gl, Z, Wm
+    //  two-sided variant: G, Gr = gR_{l+1}, Wk, W1, GlB = gL_l, GpB = gL_{l-1}
+    //  both:              K, Kn (drain column factor), Rl (R_l)
+    cx<T>* G = P;
+    cx<T>* Gl = A;       // Dyson: gL_l;  two-sided: work matrix Wk
+    cx<T>* Z = X;        // Dyson: Z;     two-sided: W1
+    cx<T>* Wm = M3;      // Dyson: Wm;    two-sided: Gr
+    cx<T>* GlB = M4;     // two-sided only
+    cx<T>* GpB = M5;     // two-sided only
+    cx<T>* K = (R == V0) ? V1 : V0;
+    cx<T>* Kn = V2;
+    cx<T>* Rl = R;
     if (real) {
       // K_{L-1} = G_{L-1,L-1} L_D: K[r][j] = sum_s G[r][site_s] w^{j s} sqrt(gamma_j/m)
-      for (int o = lane; o < b * mD; o += 32) {
+      for (int o = tid; o < b * mD; o += NT) {
         const int r = o / mD, j = o - r * mD;
-        cd acc = czero();
+        cx<T> acc = cz<T>();
         for (int s = 0; s < mD; ++s) {
           const int e = (j * s) % mD;
-          acc = cmac(acc, G[r * b + LD.sites[s]], mk(LD.tw[2 * e], LD.tw[2 * e + 1]));
+          acc = cmac(acc, G[r * b + LD.sites[s]], tc<T>(mk(LD.tw[2 * e], LD.tw[2 * e + 1])));
         }
-        K[o] = scale(acc, sqD[j].re);
+        K[o] = scale(acc, (T)sqD[j]);
       }
-      __syncwarp();
+      csync<NW>();
     }
-    double Tval = 0.0;
+    if (TWO && L > 1) {
+      // gR_{L-1} = alpha_{L-1}^{-1} (into Wm), gL_{L-2} into GlB
+      alpha_minus<T, NW>(Wm, nullptr, L - 1, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);
+      binv<T, NW>(Wm, b, col, perm, redf, redi, tid);
+      const cx<T>* sg = reinterpret_cast<const cx<T>*>(stage + (long long)(L - 2) * lstride);
+      for (int o = tid; o < nn; o += NT) GlB[o] = sg[o];
+      csync<NW>();
+    }
+    double rnum = 0.0, rden = 0.0;   // sum-rule residual: max |A_S + A_D + 2 Im G| / max |2 Im G|
     for (int l = L - 1; l >= 0; --l) {
       if (l < L - 1) {
-        const cd* sg = reinterpret_cast<const cd*>(stage + (long long)l * lstride);
-        for (int o = lane; o < nn; o += 32) Gl[o] = sg[o];
-        if (real)
-          for (int o = lane; o < b * mS; o += 32) Rl[o] = sg[bb + o];
-        __syncwarp();
+        const cx<T>* sg = reinterpret_cast<const cx<T>*>(stage + (long long)l * lstride);
         const int* ccnt = C.cs_cnt + (long long)l * b;
         const int* cidx = C.cs_idx + (long long)l * b * kmax;
         const cd* cval = C.cs_val + (long long)l * b * kmax;
-        // Z = gL_l H_{l,l+1}
-        times_hup(Z, Gl, b, b, ccnt, cidx, cval, kmax, lane);
-        __syncwarp();
-        if (real) wgemm(Kn, mD, Z, b, K, mD, b, b, mD, nullptr, 0, lane);
-        // Wm = Z G_{l+1}
-        wgemm(Wm, b, Z, b, G, b, b, b, b, nullptr, 0, lane);
-        __syncwarp();
-        // Z = H_{l+1,l} gL_l
-        hdn_times(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, lane);
-        __syncwarp();
-        // G = gL_l + Wm Z
-        wgemm(G, b, Wm, b, Z, b, b, b, b, Gl, b, lane);
-        __syncwarp();
+        if (!TWO) {
+          for (int o = tid; o < nn; o += NT) Gl[o] = sg[o];
+          if (real)
+            for (int o = tid; o < b * mS; o += NT) Rl[o] = sg[bb + o];
+          csync<NW>();
+          times_hup<T, NT>(Z, Gl, b, b, ccnt, cidx, cval, kmax, tid);                // Z = gL_l H_{l,l+1}
+          csync<NW>();
+          if (real) bgemm<T, NT>(Kn, mD, Z, b, K, mD, b, b, mD, nullptr, 0, tid);    // K_l = Z K_{l+1}
+          bgemm<T, NT>(Wm, b, Z, b, G, b, b, b, b, nullptr, 0, tid);                 // Wm = Z G_{l+1}
+          csync<NW>();
+          hdn_times<T, NT>(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, tid);             // Z = H_{l+1,l} gL_l
+          csync<NW>();
+          bgemm<T, NT>(G, b, Wm, b, Z, b, b, b, b, Gl, b, tid);                       // G = gL_l + Wm Z
+          csync<NW>();
+        } else {
+          // G_ll = (alpha_l - x_l - y_l)^{-1} with x_l = H_{l,l+1} gR_{l+1} H_{l+1,l} and
+          // y_l = H_{l,l-1} gL_{l-1} H_{l-1,l}: no cancellation between large terms
+          cx<T>* Wk = Gl;
+          cx<T>* W1 = Z;
+          cx<T>* Gr = Wm;
+          const int* rcnt = C.rs_cnt + (long long)l * b;
+          const int* ridx = C.rs_idx + (long long)l * b * kmax;
+          const cd* rval = C.rs_val + (long long)l * b * kmax;
+          if (real)
+            for (int o = tid; o < b * mS; o += NT) Rl[o] = sg[bb + o];
+          if (l > 0) {
+            const cx<T>* sp = reinterpret_cast<const cx<T>*>(stage + (long long)(l - 1) * lstride);
+            for (int o = tid; o < nn; o += NT) GpB[o] = sp[o];
+          }
+          hup_times<T, NT>(W1, Gr, b, b, b, rcnt, ridx, rval, kmax, tid);             // H_{l,l+1} gR_{l+1}
+          if (real) times_hup<T, NT>(Z == W1 ? Wk : Wk, GlB, b, b, ccnt, cidx, cval, kmax, tid);  // gL_l H_{l,l+1}
+          csync<NW>();
+          if (real) bgemm<T, NT>(Kn, mD, Wk, b, K, mD, b, b, mD, nullptr, 0, tid);   // K_l = gL_l H K_{l+1}
+          times_hdn<T, NT>(G, W1, b, b, rcnt, ridx, rval, kmax, tid);                  // x_l (into G)
+          csync<NW>();
+          alpha_minus<T, NW>(Gr, G, l, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);  // alpha_l - x_l
+          if (l > 0) {
+            const int* pcnt = C.cs_cnt + (long long)(l - 1) * b;
+            const int* pidx = C.cs_idx + (long long)(l - 1) * b * kmax;
+            const cd* pval = C.cs_val + (long long)(l - 1) * b * kmax;
+            hdn_times<T, NT>(W1, GpB, b, b, b, pcnt, pidx, pval, kmax, tid);          // H_{l,l-1} gL_{l-1}
+            csync<NW>();
+            times_hup<T, NT>(Wk, W1, b, b, pcnt, pidx, pval, kmax, tid);              // y_l
+            csync<NW>();
+            for (int o = tid; o < nn; o += NT) G[o] = Gr[o] - Wk[o];
+          } else {
+            for (int o = tid; o < nn; o += NT) G[o] = Gr[o];
+          }
+          csync<NW>();
+          binv<T, NW>(G, b, col, perm, redf, redi, tid);                              // G_ll
+          if (l > 0) binv<T, NW>(Gr, b, col, perm, redf, redi, tid);                  // gR_l
+          cx<T>* t = GlB;
+          GlB = GpB;
+          GpB = t;
+        }
         if (real) {
-          cd* t = K;
+          cx<T>* t = K;
           K = Kn;
           Kn = t;
         }
       }
       // per-site contributions of layer l, summed per ring
       double vr[2] = {0.0, 0.0};
+      cx<T>* Pm = TWO ? Z : Wm;   // free b x m buffer for G_ll R_l
       if (real) {
-        // Pm = G_ll R_l into Wm, then row norms
-        wgemm(Wm, mS, G, b, Rl, mS, b, b, mS, nullptr, 0, lane);
-        __syncwarp();
-        for (int r = lane; r < b; r += 32) {
-          double as = 0.0, ad = 0.0;
-          for (int j = 0; j < mS; ++j) as += abs2(Wm[r * mS + j]);
+        bgemm<T, NT>(Pm, mS, G, b, Rl, mS, b, b, mS, nullptr, 0, tid);               // G_ll R_l
+        csync<NW>();
+        for (int r = tid; r < b; r += NT) {
+          T as = T(0), ad = T(0);
+          for (int j = 0; j < mS; ++j) as += abs2(Pm[r * mS + j]);
           for (int j = 0; j < mD; ++j) ad += abs2(K[r * mD + j]);
-          vr[r / spr] += wS * as + wD * ad;
+          vr[r / spr] += wS * (double)as + wD * (double)ad;
+          if (a.resid) {
+            const double gim = (double)G[r * b + r].im;
+            rnum = fmax(rnum, fabs((double)as + (double)ad + 2.0 * gim));
+            rden = fmax(rden, fabs(2.0 * gim));
+          }
         }
       } else {
-        for (int r = lane; r < b; r += 32) {
-          const cd gd = G[r * b + r];
-          vr[r / spr] += kap.re * gd.im + kap.im * gd.re;
+        for (int r = tid; r < b; r += NT) {
+          const cx<T> gd = G[r * b + r];
+          vr[r / spr] += kap.re * (double)gd.im + kap.im * (double)gd.re;
         }
       }
       for (int q = 0; q < rpb; ++q) {
-        const double s = warp_sum(vr[q]);
-        if (lane == 0) part[l * rpb + q] = s;
+        const double s = bsum<NW>(vr[q], redd, tid);
+        if (tid == 0) part[l * rpb + q] = s;
       }
-      __syncwarp();
+      csync<NW>();
     }
     if (real) {
       // T = || L_S^dag K_0 ||_F^2, (L_S^dag K_0)[i][j] = sum_s conj(L_S[site_s][i]) K_0[site_s][j]
       double tv = 0.0;
-      for (int o = lane; o < mS * mD; o += 32) {
+      for (int o = tid; o < mS * mD; o += NT) {
         const int i = o / mD, j = o - i * mD;
-        cd acc = czero();
+        cx<T> acc = cz<T>();
         for (int s = 0; s < mS; ++s) {
           const int e = (i * s) % mS;
-          acc = cmac_cj(acc, mk(LS.tw[2 * e], LS.tw[2 * e + 1]), K[LS.sites[s] * mD + j]);
+          acc = cmac_cj(acc, tc<T>(mk(LS.tw[2 * e], LS.tw[2 * e + 1])), K[LS.sites[s] * mD + j]);
         }
-        tv += abs2(acc) * sqS[i].re * sqS[i].re;
+        tv += (double)abs2(acc) * sqS[i] * sqS[i];
       }
-      Tval = warp_sum(tv);
-      if (lane == 0) a.Tpart[W.tout] = Tval;
+      const double Tval = bsum<NW>(tv, redd, tid);
+      if (tid == 0) a.Tpart[W.tout] = Tval;
+      if (a.resid) {
+        const double rn = cta_max<NW>(rnum, redd, tid);
+        const double rd = cta_max<NW>(rden, redd, tid);
+        if (tid == 0) a.resid[W.tout] = rn / fmax(rd, 1e-300);
+      }
+      if (a.growth) {
+        const double gm = cta_max<NW>((double)gmax, redd, tid);
+        if (tid == 0) a.growth[W.tout] = sqrt(gm);
+      }
     }
-    __syncwarp();
+    csync<NW>();
   }
 }
 
-int launch_sweep_blk_f64(const SweepArgs& a, int b_max, int m_max, int grid, int warps,
-                         cudaStream_t s) {
-  // the dynamic shared memory limit was raised by sweep_blk_occupancy when planning
-  const size_t smem = sweep_blk_smem_bytes(b_max, m_max, warps);
-  sweep_blk_kernel<<<grid, warps * 32, smem, s>>>(a, b_max, m_max);
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
-
-}  // namespace negf
-
-namespace negf {
-int sweep_blk_occupancy(int warps, size_t smem) {
-  cudaFuncSetAttribute(sweep_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename T, int NW>
+static int blk_occupancy(size_t smem) {
+  constexpr bool TWO = sizeof(T) == 4;
+  cudaFuncSetAttribute(sweep_blk_kernel<T, NW, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_blk_kernel, warps * 32, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_blk_kernel<T, NW, TWO>, 32 * NW, smem) != cudaSuccess ||
       per < 1) {
     cudaGetLastError();
     per = 1;
   }
   return per;
 }
+
+int sweep_blk_occupancy_t(bool fp32, int warps, size_t smem) {
+  if (fp32) {
+    if (warps == 1) return blk_occupancy<float, 1>(smem);
+    if (warps == 2) return blk_occupancy<float, 2>(smem);
+    return blk_occupancy<float, 4>(smem);
+  }
+  if (warps == 1) return blk_occupancy<double, 1>(smem);
+  if (warps == 2) return blk_occupancy<double, 2>(smem);
+  return blk_occupancy<double, 4>(smem);
+}
+int sweep_blk_occupancy(int warps, size_t smem) { return sweep_blk_occupancy_t(false, warps, smem); }
+
+int launch_sweep_blk_t(bool fp32, const SweepArgs& a, int b_max, int m_max, int grid, int warps, cudaStream_t s) {
+  // the dynamic shared memory limit was raised by the occupancy query when planning
+  const size_t smem = sweep_blk_smem_bytes_t(b_max, m_max, fp32 ? 8 : 16);
+  if (fp32) {
+    if (warps == 1)
+      sweep_blk_kernel<float, 1, true><<<grid, 32, smem, s>>>(a, b_max, m_max);
+    else if (warps == 2)
+      sweep_blk_kernel<float, 2, true><<<grid, 64, smem, s>>>(a, b_max, m_max);
+    else
+      sweep_blk_kernel<float, 4, true><<<grid, 128, smem, s>>>(a, b_max, m_max);
+  } else {
+    if (warps == 1)
+      sweep_blk_kernel<double, 1, false><<<grid, 32, smem, s>>>(a, b_max, m_max);
+    else if (warps == 2)
+      sweep_blk_kernel<double, 2, false><<<grid, 64, smem, s>>>(a, b_max, m_max);
+    else
+      sweep_blk_kernel<double, 4, false><<<grid, 128, smem, s>>>(a, b_max, m_max);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_sweep_blk_f64(const SweepArgs& a, int b_max, int m_max, int grid, int warps, cudaStream_t s) {
+  return launch_sweep_blk_t(false, a, b_max, m_max, grid, warps, s);
+}
+
 }  // namespace negf

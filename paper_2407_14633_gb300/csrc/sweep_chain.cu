@@ -97,7 +97,10 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
     cx<T> gl = mk(T(0), T(0));
     T rl = T(0);              // |gL_l|^2
     T ql = (T)(wS * gamS);    // (g w fS / 2pi) Gamma_S |Q_l|^2
-    const int nf = (W.kind == 0) ? 4 : 2;
+    const bool want_r = a.resid != nullptr && W.kind == 0;
+    T qu = T(1);              // |Q_l|^2 (residual only)
+    T rmaxg = T(0);           // largest |gL_l|^2 (growth diagnostic)
+    const int nf = (W.kind == 0) ? (want_r ? 5 : 4) : 2;
     for (int l = 0; l < L; ++l) {
       const cd h = Hd[l];
       cx<T> x = mk((T)(eps.re - h.re - U[l]), (T)(eps.im - h.im));
@@ -109,22 +112,27 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
         x.re = fma(-hs, gl.re, x.re);
         x.im = fma(-hs, gl.im, x.im);
         if (W.kind == 0) ql = hs * rl * ql;
+        if (want_r) qu = hs * rl * qu;
       }
       const T r = T(1) / fma(x.re, x.re, x.im * x.im);
       gl = mk(x.re * r, -x.im * r);
       rl = r;
+      rmaxg = r > rmaxg ? r : rmaxg;
       T* s = st + (long long)l * nf * 32;
       s[lane] = gl.re;
       s[32 + lane] = gl.im;
       if (W.kind == 0) {
         s[64 + lane] = r;
         s[96 + lane] = ql;
+        if (want_r) s[128 + lane] = qu;
       }
     }
 
     // ---------------- backward sweep
     cx<T> G = gl;             // G_{L-1,L-1}
     T c = abs2(G);            // |G_{l,L-1}|^2
+    // sum-rule residual of the lane: max_l |A_S + A_D + 2 Im G|_ll / max_l |2 Im G_ll|
+    double rnum = 0.0, rden = 0.0;
     for (int l = L - 1; l >= 0; --l) {
       const T* s = st + (long long)l * nf * 32;
       if (l < L - 1) {
@@ -138,6 +146,13 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
       if (W.kind == 0) {
         const T q = s[96 + lane];
         v = (double)(q * abs2(G)) + wD * gamD * (double)c;
+        if (want_r) {
+          // A_S + A_D + 2 Im G <= 0 up to rounding (equality up to 2 eta |G|^2 terms)
+          const double as = gamS * (double)s[128 + lane] * (double)abs2(G);
+          const double gim = (double)G.im;
+          rnum = fmax(rnum, fabs(as + gamD * (double)c + 2.0 * gim));
+          rden = fmax(rden, fabs(2.0 * gim));
+        }
       } else {
         v = kap.re * (double)G.im + kap.im * (double)G.re;
       }
@@ -147,7 +162,11 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
         flush_rings(red, lane, cnt, part + l);
       }
     }
-    if (W.kind == 0 && act) a.Tpart[W.tout + lane] = gamS * gamD * (double)c;
+    if (W.kind == 0 && act) {
+      a.Tpart[W.tout + lane] = gamS * gamD * (double)c;
+      if (want_r) a.resid[W.tout + lane] = rnum / fmax(rden, 1e-300);
+      if (a.growth) a.growth[W.tout + lane] = sqrt((double)rmaxg);
+    }
   }
 }
 
@@ -237,6 +256,7 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
     // forward: gL_l and R_l = Q_l L_S (a 2-vector, L_S = sqrt(Gamma_S) e_siteS)
     m2<T> gl;
     cx<T> R[2];
+    T gmax2 = T(0);   // largest |gL_l entry|^2 (growth diagnostic)
     for (int l = 0; l < L; ++l) {
       m2<T> A = load2<T>(C.Hdiag + (long long)l * 4, false);
 #pragma unroll
@@ -268,6 +288,10 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
         Rn[siteS] = mk(lS, T(0));
       }
       gl = inv2(A);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) gmax2 = abs2(gl.a[i][j]) > gmax2 ? abs2(gl.a[i][j]) : gmax2;
       R[0] = Rn[0];
       R[1] = Rn[1];
       T* s = st + (long long)l * NF * 32;
@@ -288,6 +312,8 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
     }
 
     // backward: G_ll, K_l = G_{l,L-1} L_D, P_l = G_ll R_l
+    const bool want_r = a.resid != nullptr && W.kind == 0;
+    double rnum = 0.0, rden = 0.0;   // sum-rule residual, as in the 1 x 1 sweep
     m2<T> G = gl;
     cx<T> K[2];
     K[0] = scale(G.a[0][siteD], lD);
@@ -327,6 +353,12 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
         cx<T> P1 = cmac(G.a[1][0] * Rl[0], G.a[1][1], Rl[1]);
         v0 = wS * (double)abs2(P0) + wD * (double)abs2(K[0]);
         v1 = wS * (double)abs2(P1) + wD * (double)abs2(K[1]);
+        if (want_r) {
+          const double g0 = (double)G.a[0][0].im, g1 = (double)G.a[1][1].im;
+          rnum = fmax(rnum, fabs((double)abs2(P0) + (double)abs2(K[0]) + 2.0 * g0));
+          rnum = fmax(rnum, fabs((double)abs2(P1) + (double)abs2(K[1]) + 2.0 * g1));
+          rden = fmax(rden, fmax(fabs(2.0 * g0), fabs(2.0 * g1)));
+        }
       } else {
         v0 = kap.re * (double)G.a[0][0].im + kap.im * (double)G.a[0][0].re;
         v1 = kap.re * (double)G.a[1][1].im + kap.im * (double)G.a[1][1].re;
@@ -347,6 +379,8 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
     if (W.kind == 0 && act) {
       // T = Tr[Gamma_S G_{0,L-1} Gamma_D G_{0,L-1}^dag] = Gamma_S |K_0[siteS]|^2
       a.Tpart[W.tout + lane] = gamS * (double)abs2(K[siteS]);
+      if (want_r) a.resid[W.tout + lane] = rnum / fmax(rden, 1e-300);
+      if (a.growth) a.growth[W.tout + lane] = sqrt((double)gmax2);
     }
   }
 }
@@ -368,12 +402,19 @@ int launch_sweep_b1_f32(const SweepArgs& a, int grid, int block, cudaStream_t s)
 int launch_sweep_b2_f64(const SweepArgs& a, int grid, int block, cudaStream_t s) {
   return launch_common(sweep_b2_kernel<double>, a, grid, block, s);
 }
+int launch_sweep_b2_f32(const SweepArgs& a, int grid, int block, cudaStream_t s) {
+  return launch_common(sweep_b2_kernel<float>, a, grid, block, s);
+}
 
 }  // namespace negf
 
 namespace negf {
 int sweep_chain_occupancy(int cls, int threads, size_t smem) {
-  void (*k)(SweepArgs) = cls == 0 ? sweep_b1_kernel<double> : sweep_b2_kernel<double>;
+  return sweep_chain_occupancy_t(false, cls, threads, smem);
+}
+int sweep_chain_occupancy_t(bool fp32, int cls, int threads, size_t smem) {
+  void (*k)(SweepArgs) = fp32 ? (cls == 0 ? sweep_b1_kernel<float> : sweep_b2_kernel<float>)
+                              : (cls == 0 ? sweep_b1_kernel<double> : sweep_b2_kernel<double>);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem) != cudaSuccess || per < 1) {

@@ -24,7 +24,7 @@ _ip = C.POINTER(C.c_int)
 class Opts(C.Structure):
     _fields_ = [("device_ordinal", C.c_int), ("stream", C.c_void_p), ("hbm_budget_bytes", C.c_size_t),
                 ("precision", C.c_int), ("flag_threshold", C.c_double), ("edge_window", C.c_double),
-                ("fault_alloc_after", C.c_int)]
+                ("fault_alloc_after", C.c_int), ("growth_threshold", C.c_double)]
 
 
 class Lead(C.Structure):
@@ -46,7 +46,7 @@ class GridSpec(C.Structure):
 class Out(C.Structure):
     _fields_ = [("n", C.c_void_p), ("T", C.c_void_p), ("I", C.c_void_p), ("n_cont", C.c_void_p),
                 ("n_real_part", C.c_void_p), ("flags", C.c_void_p), ("resid", C.c_void_p),
-                ("on_device", C.c_int)]
+                ("growth", C.c_void_p), ("on_device", C.c_int)]
 
 
 class Poisson(C.Structure):
@@ -59,6 +59,13 @@ class Bias(C.Structure):
 
 class Broyden(C.Structure):
     _fields_ = [("zeta", C.c_double), ("M", C.c_int), ("tol", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("n_rings", C.c_int), ("n_tube", C.c_int), ("n_modes", C.c_int), ("modes", _ip),
+                ("t", C.c_double), ("kT", C.c_double), ("eta", C.c_double), ("E_B", C.c_double),
+                ("n_real", C.c_int), ("n_cont", C.c_int), ("bias", Bias), ("pois", Poisson),
+                ("broyden", Broyden), ("U0", _dp)]
 
 
 class ScResult(C.Structure):
@@ -100,6 +107,12 @@ _PROTOS = {
     "negf_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "negf_kernel_time": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_uint64)]),
     "negf_fp64_peak": (C.c_int, [C.c_void_p, _dp]),
+    "negf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)]),
+    "negf_serve_step": (C.c_int, [C.c_void_p, _ip]),
+    "negf_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(ScResult)]),
+    "negf_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_int, C.POINTER(ScResult)]),
+    "negf_cancel": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "negf_request_times": (C.c_int, [C.c_void_p, C.c_uint64, _dp, _dp, _dp]),
     "negf_chain1_compute_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                               _dp, _dp, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_double, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -180,9 +193,10 @@ class Context:
     """One libnegf context (negf_create / negf_destroy)."""
 
     def __init__(self, device=0, stream=None, hbm_budget=0, precision=PREC_FP64, flag_threshold=0.0,
-                 edge_window=0.0, fault_alloc_after=0):
+                 edge_window=0.0, fault_alloc_after=0, growth_threshold=0.0):
         self.lib = load()
-        o = Opts(device, stream or 0, hbm_budget, precision, flag_threshold, edge_window, fault_alloc_after)
+        o = Opts(device, stream or 0, hbm_budget, precision, flag_threshold, edge_window, fault_alloc_after,
+                 growth_threshold)
         h = C.c_void_p()
         rc = self.lib.negf_create(C.byref(h), C.byref(o))
         if rc:
@@ -283,7 +297,7 @@ class Context:
                        n_cont=np.zeros(info["n_rings"]), n_real_part=np.zeros(info["n_rings"]))
             keep.append(arr)
             outs[i] = Out(arr["n"].ctypes.data, arr["T"].ctypes.data, arr["I"].ctypes.data,
-                          arr["n_cont"].ctypes.data, arr["n_real_part"].ctypes.data, None, None, 0)
+                          arr["n_cont"].ctypes.data, arr["n_real_part"].ctypes.data, None, None, None, 0)
         ids = np.ascontiguousarray(devs, dtype=np.int32)
         self._chk(self.lib.negf_compute(self.h, _pi(ids), len(devs), outs))
         res = []
@@ -299,9 +313,26 @@ class Context:
         arr = (Out * len(devs))()
         for i, o in enumerate(outs):
             arr[i] = Out(o.get("n"), o.get("T"), o.get("I"), o.get("n_cont"), o.get("n_real_part"),
-                         None, None, 1)
+                         None, None, None, 1)
         ids = np.ascontiguousarray(devs, dtype=np.int32)
         return self._chk(self.lib.negf_compute(self.h, _pi(ids), len(devs), arr))
+
+    def compute_diag(self, dev):
+        """negf_compute of one device with the precision diagnostics (flags, resid, growth)."""
+        info = self._dev[dev]
+        N, nr = info["n_rings"], info.get("n_real", 0)
+        a = dict(n=np.zeros(N), T=np.zeros(max(nr, 1)), I=np.zeros(1), n_cont=np.zeros(N), n_real=np.zeros(N),
+                 flags=np.zeros(max(nr, 1), dtype=np.int32), resid=np.zeros(max(nr, 1)), growth=np.zeros(max(nr, 1)))
+        out = (Out * 1)()
+        out[0] = Out(a["n"].ctypes.data, a["T"].ctypes.data, a["I"].ctypes.data, a["n_cont"].ctypes.data,
+                     a["n_real"].ctypes.data, a["flags"].ctypes.data, a["resid"].ctypes.data,
+                     a["growth"].ctypes.data, 0)
+        ids = np.array([dev], dtype=np.int32)
+        self._chk(self.lib.negf_compute(self.h, _pi(ids), 1, out))
+        a["I"] = float(a["I"][0])
+        for k in ("T", "flags", "resid", "growth"):
+            a[k] = a[k][:nr]
+        return a
 
     def compute_raw(self, ids_arr, outs_arr):
         """negf_compute with pre-built ctypes arrays (no allocation in the call path)."""
@@ -388,6 +419,56 @@ class Context:
         t = C.c_double()
         self._chk(self.lib.negf_fp64_peak(self.h, C.byref(t)))
         return t.value
+
+    # ---- serving
+    def submit(self, n_rings, modes, V_DS, V_GS, n_real=2048, n_cont=64, n_tube=17, t=-2.7, kT=0.025,
+               eta=1e-6, E_B=None, kappa=None, dx_nm=0.1065, lam_nm=3.0, phi_gate=0.0, zeta=0.1, M=64,
+               tol=1e-8, U0=None):
+        m = np.ascontiguousarray(modes, dtype=np.int32)
+        u0 = _f64(U0, n_rings) if U0 is not None else None
+        if E_B is None:
+            E_B = -V_DS - 3.0 * abs(t) - 1.0
+        if kappa is None:
+            kappa = poisson_kappa()
+        q = Request(n_rings, n_tube, m.size, _pi(m), t, kT, eta, E_B, n_real, n_cont, Bias(V_DS, V_GS),
+                    Poisson(kappa, dx_nm, lam_nm, phi_gate), Broyden(zeta, M, tol), _p(u0))
+        tk = C.c_uint64()
+        self._chk(self.lib.negf_submit(self.h, C.byref(q), C.byref(tk)))
+        self._req = getattr(self, "_req", {})
+        self._req[tk.value] = dict(n_rings=n_rings, n_real=n_real, M=M)
+        return tk.value
+
+    def serve_step(self):
+        n = C.c_int()
+        self._chk(self.lib.negf_serve_step(self.h, C.byref(n)))
+        return n.value
+
+    def _result(self, ticket, fn, *args):
+        info = self._req[ticket]
+        N, nr, M = info["n_rings"], info["n_real"], info["M"]
+        n, U, T, hist = np.zeros(N), np.zeros(N), np.zeros(nr), np.zeros(M)
+        r = ScResult(_p(n), _p(U), _p(T), _p(hist), 0.0, 0, 0)
+        rc = fn(self.h, C.c_uint64(ticket), *args, C.byref(r))
+        if rc == EBUSY:
+            return None
+        if rc not in (OK, ENOTCONVERGED):
+            self._chk(rc)
+        return dict(status=rc, n=n, U=U, T=T, history=hist[:min(r.iterations, M)], I=r.I,
+                    converged=bool(r.converged), iterations=r.iterations)
+
+    def poll(self, ticket):
+        return self._result(ticket, self.lib.negf_poll)
+
+    def wait(self, ticket, timeout_ms=600000):
+        return self._result(ticket, self.lib.negf_wait, C.c_int(timeout_ms))
+
+    def cancel(self, ticket):
+        self._chk(self.lib.negf_cancel(self.h, C.c_uint64(ticket)))
+
+    def request_times(self, ticket):
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        self._chk(self.lib.negf_request_times(self.h, C.c_uint64(ticket), C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
 
     def launch_count(self):
         v = C.c_uint64()

@@ -1,0 +1,81 @@
+"""Mixed-precision path: complex64 sweep of the real-axis lanes, FP64 contour lanes, FP64
+recompute of flagged energies (sum-rule residual above the threshold, or a lead subband
+edge within the window).  Errors are measured against the FP64 oracle per output; the
+bounds stated here are the ones the design doc quotes."""
+import numpy as np
+import pytest
+
+from paper_2407_14633_gb300 import synth
+from tests.cases import case_params, current_err, rel_inf, run_lib, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+MIXED_BOUND = 2e-5     # n, T, I relative (norm-wise) of the mixed path
+FP32_BOUND = 1e-3      # pure complex64 sweep (no recompute)
+
+
+def ctx_with(prec, **kw):
+    from paper_2407_14633_gb300 import negf
+    return negf.Context(precision=prec, **kw)
+
+
+def workloads():
+    N = 40
+    return [
+        case_params("real", N, 96, 16, synth.sinusoid_profile(N, 4), mu_D=-0.1, n_tube=17, U_S=0.0, U_D=0.0),
+        case_params("mode", 64, 128, 16, synth.ramp_barrier(64), modes=(6, 5)),
+        case_params("mode", 64, 96, 16, synth.ramp_barrier(64), modes=(6,), cells=True),
+    ]
+
+
+@pytest.mark.parametrize("i", range(3))
+def test_mixed_precision_error_bound(i):
+    from paper_2407_14633_gb300 import negf
+    p = workloads()[i]
+    o = run_oracle(p, chunk=16)
+    with ctx_with(negf.PREC_MIXED, flag_threshold=1e-4, edge_window=0.02) as ctx:
+        _, r = run_lib(ctx, p)
+    g = 4.0 * len(p["modes"]) if p["kind"] == "mode" else 2.0
+    errs = (rel_inf(r["n"], o["n"]), rel_inf(r["T"], o["T"]), current_err(r["I"], o["I"], g, p["mu_S"] - p["mu_D"]))
+    print("mixed errors n %.2e T %.2e I %.2e" % errs)
+    assert max(errs) < MIXED_BOUND
+    # contour lanes stay FP64
+    assert rel_inf(r["n_cont"], o["n_cont"]) < 1e-10
+
+
+@pytest.mark.parametrize("i", range(3))
+def test_fp32_sweep_error_bound(i):
+    from paper_2407_14633_gb300 import negf
+    p = workloads()[i]
+    o = run_oracle(p, chunk=16)
+    with ctx_with(negf.PREC_FP32) as ctx:
+        _, r = run_lib(ctx, p)
+    errs = (rel_inf(r["n"], o["n"]), rel_inf(r["T"], o["T"]))
+    print("fp32 errors n %.2e T %.2e" % errs)
+    assert max(errs) < FP32_BOUND
+
+
+def test_mixed_flags_cover_band_edges():
+    from paper_2407_14633_gb300 import negf
+    import ctypes as C
+    N = 30
+    p = case_params("mode", N, 64, 8, np.zeros(N), mu_S=0.3, mu_D=0.2, modes=(6,))
+    with ctx_with(negf.PREC_MIXED, flag_threshold=1e30, edge_window=0.02) as ctx:
+        from tests.cases import lib_device, lib_grid
+        dev = lib_device(ctx, "mode", 17, -2.7, N, 0.0, 0.0, (6,))
+        ctx.set_potential(dev, np.zeros(N))
+        lib_grid(ctx, dev, p)
+        nr = 64
+        n = np.zeros(N); T = np.zeros(nr); I = np.zeros(1)
+        flags = np.zeros(nr, dtype=np.int32); resid = np.zeros(nr)
+        out = (negf.Out * 1)()
+        out[0] = negf.Out(n.ctypes.data, T.ctypes.data, I.ctypes.data, None, None, flags.ctypes.data,
+                          resid.ctypes.data, None, 0)
+        ids = np.array([dev], dtype=np.int32)
+        ctx.compute_raw(ids, out)
+        E = negf.make_grid(0.3, 0.2, 0.025, 1e-6, -10.0, nr, 8)["E"]
+    edge = abs(2.7) * abs(1 - 2 * abs(np.cos(6 * np.pi / 17)))
+    near = np.abs(np.abs(E) - edge) < 0.02
+    # every energy near the subband edge is flagged (its whole 32-energy item is recomputed)
+    assert np.all(flags[near] == 1)
+    assert np.all(resid >= 0.0)
