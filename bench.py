@@ -283,6 +283,11 @@ def run_ours(args):
         "clocks": clocks,
         "self_consistent_solve": sc,
     }
+    if args.extras and rank == 0:
+        from paper_2407_14633_gb300 import workloads
+        line["extras"] = {"batched_uneven": workloads.batched_uneven(),
+                          "mixed_precision": workloads.mixed_precision(),
+                          "serving": workloads.serving_sweep()}
     if rank == 0 and world == 1 and not args.no_cpu:
         secs, upd = cpu_sample()
         line["cpu_baseline"] = {"value": upd / secs, "unit": "ring-energy updates/s", "cores": 1,
@@ -327,6 +332,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--extras", action="store_true",
+                    help="also run the batched-uneven, mixed-precision and serving workloads")
     ap.add_argument("--profile-small", action="store_true",
                     help="reduced case of the block sweep for ncu captures")
     args = ap.parse_args()

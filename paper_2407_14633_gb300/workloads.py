@@ -1,0 +1,211 @@
+"""Runners for the batched, mixed-precision and serving workloads through the C ABI
+(used by bench.py --extras).  Timing uses the library's event-bracketed sweep time and host
+wall clock; inputs come from synth.py."""
+import time
+
+import numpy as np
+
+from . import negf, synth
+
+
+def _rel(x, ref):
+    den = np.max(np.abs(ref))
+    return float(np.max(np.abs(np.asarray(x) - ref)) / den) if den > 0 else 0.0
+
+
+def build_uneven(ctx, w, n_devices=None):
+    """The uneven batch: mode-space (17,0) devices, 1x1 or 2x2 blocks, 1-4 modes."""
+    devs = []
+    for d in w["devices"][:n_devices]:
+        N = d["N"]
+        cells = d["block"] == 2
+        dev = ctx.device_create(N, block=2 if cells else 1, rings_per_block=2 if cells else 1,
+                                n_chains=len(d["modes"]))
+        ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], list(d["modes"]), 0.0, -d["V_DS"])
+        ctx.set_potential(dev, d["U"])
+        ctx.set_grid_spec(dev, 0.0, -d["V_DS"], w["kT"], w["eta"], d["E_B"], d["n_real"], d["n_cont"])
+        devs.append(dev)
+    return devs
+
+
+def batched_uneven(reps=3):
+    """All 64 uneven devices in one negf_compute (one launch per kernel class and element
+    type), complex128 and complex64; updates counted per (ring, energy, mode)."""
+    w = synth.batched_uneven()
+    units = sum(d["N"] * len(d["modes"]) * (d["n_real"] + d["n_cont"]) for d in w["devices"])
+    out = {"devices": len(w["devices"]), "ring_energy_mode_updates": units}
+    ref = None
+    for name, prec in (("c128", negf.PREC_FP64), ("c64", negf.PREC_FP32)):
+        with negf.Context(precision=prec) as ctx:
+            t0 = time.perf_counter()
+            devs = build_uneven(ctx, w)
+            t_setup = time.perf_counter() - t0
+            res = ctx.compute(devs)
+            ctx.profile(True)
+            ctx.kernel_time()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                res = ctx.compute(devs)
+            wall = (time.perf_counter() - t0) / reps
+            ms, k = ctx.kernel_time()
+        sweep_s = ms / max(k, 1) * 1e-3
+        entry = {"updates_per_s_sweep": units / sweep_s, "sweep_ms": sweep_s * 1e3,
+                 "updates_per_s_e2e": units / wall, "e2e_ms": wall * 1e3, "setup_s": t_setup}
+        if ref is None:
+            ref = res
+        else:
+            entry["max_rel_err_n_vs_c128"] = max(_rel(a["n"], b["n"]) for a, b in zip(res, ref))
+            entry["max_rel_err_T_vs_c128"] = max(_rel(a["T"], b["T"]) for a, b in zip(res, ref))
+        out[name] = entry
+    return out
+
+
+def _fermi(x, kT):
+    return 0.5 * (1.0 - np.tanh(0.5 * np.asarray(x) / kT))
+
+
+def _edge_near(n_tube, t, E, U_lead, window):
+    """Energies within window of a subband edge of the (n,0) lead, edges
+    U_lead +- |t| |1 -+ 2 cos(pi j / n)| (the zone-centre and zone-boundary energies)."""
+    j = np.arange(n_tube)
+    b = 2.0 * abs(t) * np.abs(np.cos(np.pi * j / n_tube))
+    edges = np.concatenate([abs(t) - b, b - abs(t), abs(t) + b, -abs(t) - b])
+    d = np.min(np.abs(np.asarray(E)[:, None] - U_lead - edges[None, :]), axis=1)
+    return d < window
+
+
+def mixed_precision(tubes=(17, 26, 34), N=1024, n_energies=4096, windows=(0.02, 0.002)):
+    """Real-space (n,0) tubes, a quarter of the energies within 20 meV of a lead subband edge:
+    complex128 sweep vs the mixed path (complex64 sweep, FP64 recompute of flagged energies;
+    one run per band-edge window) vs the plain complex64 sweep; errors per output against
+    the complex128 result, and which criterion flagged how many energies."""
+    out = {}
+    thr, gthr = 1e-4, 20.0
+    for n_tube in tubes:
+        w = synth.mixed_precision(n_tube=n_tube, N=N, n_energies=n_energies)
+        E = w["E"]
+        wts = np.full(E.size, 2.0 / E.size)
+        fS, fD = _fermi(E - w["mu_S"], w["kT"]), _fermi(E - w["mu_D"], w["kT"])
+        E_B = float(np.min(w["U"]) - 3.0 * abs(w["t"]) - 1.0)
+        cg = negf.make_grid(w["mu_S"], w["mu_D"], w["kT"], w["eta"], E_B, 1, 64, E_min=-1.0, E_max=1.0)
+        runs = [("c128", negf.PREC_FP64, {})] + \
+            [("mixed_w%g" % win, negf.PREC_MIXED, dict(flag_threshold=thr, growth_threshold=gthr, edge_window=win))
+             for win in windows] + [("c64", negf.PREC_FP32, {})]
+        res = {}
+        for name, prec, kw in runs:
+            with negf.Context(precision=prec, **kw) as ctx:
+                dev = ctx.device_create(N, block=n_tube, rings_per_block=1, n_chains=1)
+                ctx.build_cnt_realspace(dev, n_tube, w["t"], w["U_S"], w["U_D"])
+                ctx.set_potential(dev, w["U"])
+                ctx.set_grid(dev, E, wts, fS, fD, w["eta"], cg["z"], cg["c"])
+                ctx.profile(True)
+                ctx.kernel_time()
+                t0 = time.perf_counter()
+                r = ctx.compute_diag(dev)
+                wall = time.perf_counter() - t0
+                ms, _ = ctx.kernel_time()
+            r["sweep_ms"], r["wall_s"] = ms, wall
+            res[name] = r
+        ref = res["c128"]
+        Tmax = float(np.max(np.abs(ref["T"])))
+        entry = {"c128_sweep_ms": ref["sweep_ms"]}
+        c64 = res["c64"]
+        by_resid = ~(c64["resid"] <= thr)
+        by_growth = ~(c64["growth"] <= gthr)
+        entry["c64_residual_quantiles"] = {q: float(np.nanpercentile(c64["resid"], float(q)))
+                                           for q in ("50", "90", "99")}
+        entry["flagged_by_residual"] = float(np.mean(by_resid))
+        entry["flagged_by_growth"] = float(np.mean(by_growth))
+        entry["c64_T_err_unflagged_by_residual_growth"] = float(
+            np.max(np.abs(c64["T"] - ref["T"])[~(by_resid | by_growth)], initial=0.0) / Tmax)
+        for name, _, kw in runs[1:]:
+            r = res[name]
+            dI = abs(r["I"] - ref["I"]) / max(abs(ref["I"]), 1e-30)
+            e = {"sweep_ms": r["sweep_ms"], "speedup_vs_c128": ref["sweep_ms"] / r["sweep_ms"],
+                 "rel_err_n": _rel(r["n"], ref["n"]), "rel_err_T": _rel(r["T"], ref["T"]), "rel_err_I": dI}
+            if name.startswith("mixed"):
+                near = _edge_near(n_tube, w["t"], E, w["U_S"], kw["edge_window"])
+                e["edge_window_eV"] = kw["edge_window"]
+                e["recomputed_fraction"] = float(np.mean(r["flags"]))
+                e["flagged_by_edge_window"] = float(np.mean(near))
+            entry[name] = e
+        out["(%d,0)" % n_tube] = entry
+    return out
+
+
+def serving_sweep(n_requests=256, rate_factor=2.0, tol=1e-5, M=64):
+    """256 self-consistent I-V requests: a sequential loop of negf_sc_solve calls, then the
+    continuous-batching server with Poisson arrivals at rate_factor x the sequential rate,
+    then the server with every request queued at once (its capacity).  tol is the
+    convergence threshold of Alg. 3 (1e-5)."""
+    w = synth.serving_sweep(n_requests=n_requests)
+    reqs = w["requests"]
+    kappa = negf.poisson_kappa()
+    # sequential baseline: one solve at a time on the GPU
+    seq_lat = []
+    seq_res = []
+    with negf.Context() as ctx:
+        t_all = time.perf_counter()
+        for q in reqs:
+            t0 = time.perf_counter()
+            dev = ctx.device_create(q["N"], n_chains=len(q["modes"]))
+            ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], list(q["modes"]), 0.0, -q["V_DS"])
+            E_B = -q["V_DS"] - 3.0 * abs(w["t"]) - 1.0
+            ctx.set_grid_spec(dev, 0.0, -q["V_DS"], w["kT"], w["eta"], E_B, q["n_real"], q["n_cont"])
+            U0 = np.linspace(0.0, -q["V_DS"], q["N"])
+            r = ctx.sc_solve(dev, q["V_DS"], q["V_GS"], U0, kappa, M=M, tol=tol, check=False)
+            ctx.device_destroy(dev)
+            seq_lat.append(time.perf_counter() - t0)
+            seq_res.append(r)
+        seq_total = time.perf_counter() - t_all
+    seq_rate = n_requests / seq_total
+    # served: Poisson arrivals
+    arrivals = np.cumsum(w["unit_gaps"]) / (rate_factor * seq_rate)
+    lat = []
+    served = []
+    with negf.Context() as ctx:
+        t0 = time.perf_counter()
+        tickets = [None] * n_requests
+        nxt = 0
+        done = 0
+        while done < n_requests:
+            now = time.perf_counter() - t0
+            while nxt < n_requests and arrivals[nxt] <= now:
+                q = reqs[nxt]
+                tickets[nxt] = ctx.submit(q["N"], list(q["modes"]), q["V_DS"], q["V_GS"], n_real=q["n_real"],
+                                          n_cont=q["n_cont"], tol=tol, M=M,
+                                          U0=np.linspace(0.0, -q["V_DS"], q["N"]))
+                nxt += 1
+            active = ctx.serve_step()
+            done = sum(1 for t in tickets[:nxt] if t is not None and ctx.poll(t) is not None)
+            if active == 0 and done < nxt:
+                continue
+            if active == 0 and nxt < n_requests and done == nxt:
+                time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+        total = time.perf_counter() - t0
+        for i, tk in enumerate(tickets):
+            ts, tst, td = ctx.request_times(tk)
+            lat.append(td - ts)
+            served.append(ctx.poll(tk))
+    # capacity: all requests queued at t = 0
+    with negf.Context() as ctx:
+        t0 = time.perf_counter()
+        tks = [ctx.submit(q["N"], list(q["modes"]), q["V_DS"], q["V_GS"], n_real=q["n_real"],
+                          n_cont=q["n_cont"], tol=tol, M=M, U0=np.linspace(0.0, -q["V_DS"], q["N"]))
+               for q in reqs]
+        steps = 0
+        while any(ctx.poll(t) is None for t in tks):
+            ctx.serve_step()
+            steps += 1
+        sat_total = time.perf_counter() - t0
+        sat = [ctx.poll(t) for t in tks]
+    same = sum(1 for a, b, c in zip(seq_res, served, sat) if a["iterations"] == b["iterations"] == c["iterations"]
+               and np.array_equal(a["n"], b["n"]) and np.array_equal(a["n"], c["n"]))
+    return {"requests": n_requests, "sequential_bias_points_per_s": seq_rate,
+            "sequential_p50_s": float(np.percentile(seq_lat, 50)), "sequential_p99_s": float(np.percentile(seq_lat, 99)),
+            "served_bias_points_per_s": n_requests / total, "served_p50_s": float(np.percentile(lat, 50)),
+            "served_p99_s": float(np.percentile(lat, 99)), "arrival_rate_per_s": rate_factor * seq_rate,
+            "converged": int(sum(r["converged"] for r in served)),
+            "saturated_bias_points_per_s": n_requests / sat_total, "saturated_steps": steps,
+            "bitwise_same_as_sequential": same, "tol": tol,
+            "mean_iterations": float(np.mean([r["iterations"] for r in served]))}
