@@ -271,7 +271,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_rings": N, "block": 17, "energies_real": n_real,
                    "energies_contour": n_cont, "step": "one self-consistent iteration (captured graph)",
-                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas per rank (weak)"},
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas per rank (weak)",
+                   "cta_warps": ctx.blk_width(17, 17)},
         "e2e": {"value": units_per_step / t_e2e, "unit": "ring-energy updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "call": "negf_set_potential + negf_compute, host buffers"},
         "gpu_launches": int(launches),
@@ -285,9 +286,10 @@ def run_ours(args):
     }
     if args.extras and rank == 0:
         from paper_2407_14633_gb300 import workloads
-        line["extras"] = {"batched_uneven": workloads.batched_uneven(),
-                          "mixed_precision": workloads.mixed_precision(),
-                          "serving": workloads.serving_sweep()}
+        runs = {"batched_uneven": workloads.batched_uneven, "mixed_precision": workloads.mixed_precision,
+                "serving": workloads.serving_sweep}
+        pick = list(runs) if args.extras == "all" else args.extras.split(",")
+        line["extras"] = {k: runs[k]() for k in pick}
     if rank == 0 and world == 1 and not args.no_cpu:
         secs, upd = cpu_sample()
         line["cpu_baseline"] = {"value": upd / secs, "unit": "ring-energy updates/s", "cores": 1,
@@ -307,7 +309,7 @@ def run_profile_small(args):
     from paper_2407_14633_gb300 import negf, synth
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ctx = negf.Context(device=0, stream=stream.cuda_stream)
+    ctx = negf.Context(device=0, stream=stream.cuda_stream, blk_warps=args.blk_warps)
     w = synth.realspace_17(N=128, n_real=576, n_cont=32)
     dev = ctx.device_create(w["N"], block=17, rings_per_block=1, n_chains=1)
     ctx.build_cnt_realspace(dev, 17, w["t"], w["U_S"], w["U_D"])
@@ -319,7 +321,7 @@ def run_profile_small(args):
     ms, k = ctx.kernel_time()
     flops = algorithmic_flops(17, 17, 1.5, w["N"], w["n_real"], w["n_cont"])
     print(json.dumps({"case": "profile_small", "sweep_ms": ms / k, "tflops": flops / (ms / k * 1e-3) / 1e12,
-                      "I": r["I"]}))
+                      "I": r["I"], "cta_warps": args.blk_warps}))
     ctx.close()
     return 0
 
@@ -332,10 +334,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--extras", action="store_true",
-                    help="also run the batched-uneven, mixed-precision and serving workloads")
+    ap.add_argument("--extras", nargs="?", const="all", default=None,
+                    help="also run the batched-uneven, mixed-precision and serving workloads "
+                         "(or a comma list of batched_uneven, mixed_precision, serving)")
     ap.add_argument("--profile-small", action="store_true",
                     help="reduced case of the block sweep for ncu captures")
+    ap.add_argument("--blk-warps", type=int, default=1,
+                    help="CTA width of the block sweep in --profile-small (no tuning launches)")
     args = ap.parse_args()
     if args.profile_small:
         return run_profile_small(args)

@@ -72,7 +72,12 @@ typedef struct negf_ctx negf_ctx;
  * recomputed in FP64 (0 = default 0.02).  fault_alloc_after:
  * host-side fault injection for tests, the n-th arena allocation fails (0 = off).
  * growth_threshold: mixed precision, energies whose complex64 sweep saw a gL entry larger
- * than this (1/eV) are recomputed in FP64 (0 = default 20). */
+ * than this (1/eV) are recomputed in FP64 (0 = default 20).  blk_warps: CTA width (warps)
+ * of the sweep of ring blocks wider than 2: 0 = autotuned (each width is timed once per
+ * context on the first batch of a given element type, block size and lead width large
+ * enough to fill the GPU, then cached; smaller batches use the size policy), -1 = the size
+ * policy (1 warp up to b = 20, 2 up to 28, else 4), 1 / 2 / 4 = that width.  Results are
+ * bitwise the same for every width. */
 typedef struct {
   int device_ordinal;
   void* stream;
@@ -82,6 +87,7 @@ typedef struct {
   double edge_window;
   int fault_alloc_after;
   double growth_threshold;
+  int blk_warps;
 } negf_opts;
 
 /* Create / destroy a context on one GPU.  opts may be NULL (defaults: device 0, own
@@ -194,8 +200,9 @@ int negf_set_grid_spec(negf_ctx* ctx, int dev, const negf_grid_spec* spec);
  * optional): the two parts of n.  flags (n_real, optional, int): per-energy precision
  * flags of the mixed path (1 = recomputed in FP64).  resid (n_real, optional): per-energy
  * sum-rule residual of the complex64 sweep,
- * max_a |A_S,aa + A_D,aa + 2 Im G_aa| / max_a |2 Im G_aa| over the sites a of the chain
- * (largest over chains).  growth (n_real, optional): per-energy
+ * max(0, max_a (A_S,aa + A_D,aa + 2 Im G_aa)) / max_a |2 Im G_aa| over the sites a of the
+ * chain, largest over chains (exact arithmetic gives A_S + A_D = -2 Im G - 2 eta G G^dagger
+ * <= -2 Im G on the diagonal, so a positive excess is rounding error).  growth (n_real, optional): per-energy
  * largest entry modulus of the left-connected gL_l seen by the complex64 sweep (large
  * near resonances of the half-open chain, where the backward sweep must cancel it).  Any
  * pointer may be NULL except n.  If on_device != 0 every pointer is device memory on the
@@ -369,6 +376,10 @@ int negf_launch_count(const negf_ctx* ctx, uint64_t* launches);
  * returns (and resets) the summed sweep time in ms and the number of timed sweeps. */
 int negf_profile(negf_ctx* ctx, int enable);
 int negf_kernel_time(negf_ctx* ctx, double* sweep_ms, uint64_t* sweeps);
+
+/* The CTA width (warps) the autotuner chose for ring blocks of width b with leads of m
+ * sites in FP64 (fp32 = 0) or FP32 (fp32 = 1); NEGF_EINVAL if that shape was not tuned. */
+int negf_blk_width(negf_ctx* ctx, int fp32, int b, int m, int* warps);
 
 /* Measured FP64 FMA throughput of this GPU (TFLOP/s): a register-resident FMA loop over
  * every SM, best of three, for the FP64 roofline of the sweep kernels. */

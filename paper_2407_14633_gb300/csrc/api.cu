@@ -371,7 +371,8 @@ int negf_create(negf_ctx** out, const negf_opts* opts) {
   negf_ctx* c = new (std::nothrow) negf_ctx();
   if (!c) return NEGF_ENOMEM;
   if (opts) c->opts = *opts;
-  if (c->opts.precision < 0 || c->opts.precision > 2) {
+  const int bw = c->opts.blk_warps;
+  if (c->opts.precision < 0 || c->opts.precision > 2 || !(bw == -1 || bw == 0 || bw == 1 || bw == 2 || bw == 4)) {
     delete c;
     return NEGF_EINVAL;
   }

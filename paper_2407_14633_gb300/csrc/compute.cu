@@ -122,6 +122,81 @@ static int group_of(int cls, int b, bool f32) {
 static int group_class(int g) { return std::min(g % 5, 2); }
 static bool group_f32(int g) { return g >= 5; }
 
+static long long width_key(bool f32, int b, int m) { return ((long long)f32 << 40) | ((long long)b << 20) | m; }
+
+static SweepArgs group_args(const Plan& P, int g, const int* order, int n, double* resid, double* growth) {
+  const PlanBufs& B = *P.bufs;
+  SweepArgs a;
+  a.devs = (const DeviceView*)B.views.p;
+  a.items = (const WorkItem*)B.items.p;
+  a.order = order;
+  a.n_items = n;
+  a.counter = (int*)B.counter.p + g;
+  a.partial = (double*)B.partial.p;
+  a.Tpart = (double*)B.tpart.p;
+  a.resid = resid;
+  a.growth = growth;
+  a.stage = (unsigned char*)B.stage.p;
+  a.stage_stride = P.stride[g % 5];
+  a.status = (int*)B.status.p;
+  return a;
+}
+
+// Autotuner of the CTA width of the wide-block sweep.  Every output element and every
+// reduction of that kernel has an evaluation order that does not depend on the width, so
+// the choice changes speed only.  Each candidate width (1, 2, 4 warps) runs the same first
+// items of the group, one full wave of the candidate with the most resident CTAs, once to
+// warm up and once timed with events; the fastest is cached per (element type, b, m).  The
+// trial outputs are overwritten by the real launch.
+static int tune_width(Ctx* c, Plan& P, int g) {
+  const PlanBufs& B = *P.bufs;
+  const bool f32 = group_f32(g);
+  const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16);
+  const long long stride = P.stride[g % 5];
+  const long long max_grid = stride > 0 ? (long long)(B.stage.bytes / stride) : 0;
+  const int cand[3] = {1, 2, 4};
+  int grid[3], S = 0;
+  for (int i = 0; i < 3; ++i) {
+    const int per_sm = sweep_blk_occupancy_t(f32, cand[i], sm);
+    grid[i] = per_sm > 0 ? (int)std::min<long long>(std::min<long long>((long long)c->sms * per_sm, P.ncls[g]), max_grid)
+                         : 0;
+    S = std::max(S, grid[i]);
+  }
+  if (S < 1) return NEGF_OK;
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_err(c, NEGF_ECUDA, "event creation failed");
+  float best = 0.0f;
+  int bi = -1;
+  int rc = NEGF_OK;
+  for (int rep = 0; rep < 2 && !rc; ++rep)
+    for (int i = 0; i < 3 && !rc; ++i) {
+      if (grid[i] < 1) continue;
+      const SweepArgs a = group_args(P, g, (const int*)B.order.p + P.ooff[g], S, nullptr, nullptr);
+      if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+          launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], grid[i], cand[i], s) ||
+          cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = set_err(c, NEGF_ECUDA, "width tuning launch failed");
+        break;
+      }
+      ++c->launches;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep == 1 && (bi < 0 || ms < best)) {
+        best = ms;
+        bi = i;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  c->blk_width[width_key(f32, P.gb[g], P.gm[g])] = cand[bi];
+  P.gw[g] = cand[bi];
+  P.grid[g] = std::max(1, grid[bi]);
+  return NEGF_OK;
+}
+
 int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOverride>* ov, int chain_only,
                Plan& P, PlanBufs* bufs) {
   cudaSetDevice(c->ordinal);
@@ -234,6 +309,24 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     P.ooff[g] = (int)order_all.size();
     P.ncls[g] = (int)order[g].size();
     order_all.insert(order_all.end(), order[g].begin(), order[g].end());
+  }
+
+  // CTA width of the wide-block groups: forced, cached from an earlier tuning, or the size
+  // policy (tuned at the end of this call when the group fills the GPU)
+  bool tune_g[NGROUPS] = {false};
+  cudaStreamCaptureStatus capst = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(c->stream, &capst);
+  for (int g = 0; g < NGROUPS; ++g) {
+    if (group_class(g) != 2 || !P.ncls[g]) continue;
+    if (c->opts.blk_warps > 0) {
+      P.gw[g] = c->opts.blk_warps;
+    } else if (c->opts.blk_warps == 0) {
+      auto it = c->blk_width.find(width_key(group_f32(g), P.gb[g], P.gm[g]));
+      if (it != c->blk_width.end())
+        P.gw[g] = it->second;
+      else
+        tune_g[g] = P.ncls[g] >= c->sms && capst == cudaStreamCaptureStatusNone;
+    }
   }
 
   // launch geometry and staging per group (staging sized for FP64 elements)
@@ -364,27 +457,19 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       cudaMemcpy(B.order.p, order_all.data(), sizeof(int) * n_items, cudaMemcpyHostToDevice) ||
       cudaMemcpy(B.reduce.p, rd.data(), sizeof(ReduceDev) * nd, cudaMemcpyHostToDevice))
     return set_err(c, NEGF_ECUDA, "upload of the launch plan failed");
+  for (int g = 0; g < NGROUPS; ++g)
+    if (tune_g[g]) {
+      int rc = tune_width(c, P, g);
+      if (rc) return rc;
+    }
   return NEGF_OK;
 }
 
 static int launch_group(Ctx* c, const Plan& P, int g, const int* order, int n, int grid, double* resid,
                         double* growth) {
-  const PlanBufs& B = *P.bufs;
   const int cls = group_class(g);
   const bool f32 = group_f32(g);
-  SweepArgs a;
-  a.devs = (const DeviceView*)B.views.p;
-  a.items = (const WorkItem*)B.items.p;
-  a.order = order;
-  a.n_items = n;
-  a.counter = (int*)B.counter.p + g;
-  a.partial = (double*)B.partial.p;
-  a.Tpart = (double*)B.tpart.p;
-  a.resid = resid;
-  a.growth = growth;
-  a.stage = (unsigned char*)B.stage.p;
-  a.stage_stride = P.stride[g % 5];
-  a.status = (int*)B.status.p;
+  const SweepArgs a = group_args(P, g, order, n, resid, growth);
   cudaStream_t s = c->stream;
   int rc;
   if (cls == 0)
@@ -769,6 +854,14 @@ int negf_kernel_time(negf_ctx* c, double* sweep_ms, uint64_t* sweeps) {
   *sweeps = c->prof_count;
   c->prof_ms = 0.0;
   c->prof_count = 0;
+  return NEGF_OK;
+}
+
+int negf_blk_width(negf_ctx* c, int fp32, int b, int m, int* warps) {
+  if (!c || !warps) return NEGF_EINVAL;
+  auto it = c->blk_width.find(width_key(fp32 != 0, b, m));
+  if (it == c->blk_width.end()) return NEGF_EINVAL;
+  *warps = it->second;
   return NEGF_OK;
 }
 

@@ -94,6 +94,8 @@ struct Ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   double prof_ms = 0.0;
   uint64_t prof_count = 0;
+  // CTA widths chosen by the autotuner, keyed by (element type, b, m)
+  std::map<long long, int> blk_width;
   // serving state (serve.cu)
   struct Serve* serve = nullptr;
   std::mutex serve_mu;

@@ -220,6 +220,7 @@ int step_locked(Ctx* c, Serve* s, int* n_active) {
   }
   // admit in arrival order while the budget allows
   const size_t budget = c->opts.hbm_budget_bytes;
+  bool released = false;
   while (!s->queue.empty()) {
     Req* r = s->queue.front();
     if (r->state == Q_CANCELLED) {
@@ -232,6 +233,14 @@ int step_locked(Ctx* c, Serve* s, int* n_active) {
     for (Req* q : s->active) Lmax = std::max<size_t>(Lmax, q->N);
     const size_t stage_min = Lmax * 8 * 5 * 32 * 8;
     if (budget && !s->active.empty() && s->active_bytes + need + stage_min > budget) break;
+    if (budget && !released) {
+      // the batch plan is rebuilt after admission anyway; its staging is released first so
+      // the set-up of the new request (its neutral charge) has room for its own sweep
+      cudaStreamSynchronize(c->stream);
+      free_plan_bufs(c, s->bufs);
+      s->plan_valid = false;
+      released = true;
+    }
     s->queue.pop_front();
     r->bytes = need;
     int rc = activate(c, r);

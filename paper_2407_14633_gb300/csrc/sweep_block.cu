@@ -20,9 +20,10 @@
 // in FP64 and the quadrature weights applied in FP64).  For real-axis lanes the kernel
 // can also record the lane's residual of the sum rule
 //   -2 Im G_aa = A_S,aa + A_D,aa + 2 eta (G G^dagger)_aa,
-// max_a |A_S,aa + A_D,aa + 2 Im G_aa| / max_a |2 Im G_aa| (the eta term is below rounding
-// except at states the leads do not reach), which the mixed path uses to decide which
-// energies to recompute in FP64.
+// max(0, max_a (A_S,aa + A_D,aa + 2 Im G_aa)) / max_a |2 Im G_aa|.  The eta term is not
+// available to the sweep and is never negative, so only the excess of A_S + A_D over
+// -2 Im G is a rounding error; the mixed path recomputes energies whose excess, relative
+// to the largest spectral weight of the lane, passes a threshold.
 #include "common.cuh"
 #include "lead.cuh"
 
@@ -210,19 +211,14 @@ __device__ void binv(cx<T>* A, int b, cx<T>* col, int* perm, float* rbest, int* 
   }
 }
 
-// deterministic CTA sum / max (warp butterfly, then the warps in order)
-template <int NW>
-__device__ __forceinline__ double bsum(double v, double* red, int tid) {
+// warp butterfly sum (every lane receives the total)
+__device__ __forceinline__ double wsum(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if (NW == 1) return v;
-  if ((tid & 31) == 0) red[tid >> 5] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int w = 0; w < NW; ++w) s += red[w];
-  __syncthreads();
-  return s;
+  return v;
 }
+
+// CTA max (exact in any order)
 template <int NW>
 __device__ __forceinline__ double cta_max(double v, double* red, int tid) {
 #pragma unroll
@@ -488,7 +484,7 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
       for (int o = tid; o < nn; o += NT) GlB[o] = sg[o];
       csync<NW>();
     }
-    double rnum = 0.0, rden = 0.0;   // sum-rule residual: max |A_S + A_D + 2 Im G| / max |2 Im G|
+    double rnum = 0.0, rden = 0.0;   // sum-rule residual: max(0, A_S + A_D + 2 Im G) / max |2 Im G|
     for (int l = L - 1; l >= 0; --l) {
       if (l < L - 1) {
         const cx<T>* sg = reinterpret_cast<const cx<T>*>(stage + (long long)l * lstride);
@@ -556,48 +552,53 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
           Kn = t;
         }
       }
-      // per-site contributions of layer l, summed per ring
+      // per-site contributions of layer l, summed per ring.  The row sums and ring sums run
+      // on warp 0 with a fixed lane mapping, so the result does not depend on the CTA width.
       double vr[2] = {0.0, 0.0};
       cx<T>* Pm = TWO ? Z : Wm;   // free b x m buffer for G_ll R_l
       if (real) {
         bgemm<T, NT>(Pm, mS, G, b, Rl, mS, b, b, mS, nullptr, 0, tid);               // G_ll R_l
         csync<NW>();
-        for (int r = tid; r < b; r += NT) {
-          T as = T(0), ad = T(0);
-          for (int j = 0; j < mS; ++j) as += abs2(Pm[r * mS + j]);
-          for (int j = 0; j < mD; ++j) ad += abs2(K[r * mD + j]);
-          vr[r / spr] += wS * (double)as + wD * (double)ad;
-          if (a.resid) {
-            const double gim = (double)G[r * b + r].im;
-            rnum = fmax(rnum, fabs((double)as + (double)ad + 2.0 * gim));
-            rden = fmax(rden, fabs(2.0 * gim));
+        if (tid < 32)
+          for (int r = tid; r < b; r += 32) {
+            T as = T(0), ad = T(0);
+            for (int j = 0; j < mS; ++j) as += abs2(Pm[r * mS + j]);
+            for (int j = 0; j < mD; ++j) ad += abs2(K[r * mD + j]);
+            vr[r / spr] += wS * (double)as + wD * (double)ad;
+            if (a.resid) {
+              const double gim = (double)G[r * b + r].im;
+              rnum = fmax(rnum, (double)as + (double)ad + 2.0 * gim);
+              rden = fmax(rden, fabs(2.0 * gim));
+            }
           }
-        }
-      } else {
-        for (int r = tid; r < b; r += NT) {
+      } else if (tid < 32) {
+        for (int r = tid; r < b; r += 32) {
           const cx<T> gd = G[r * b + r];
           vr[r / spr] += kap.re * (double)gd.im + kap.im * (double)gd.re;
         }
       }
-      for (int q = 0; q < rpb; ++q) {
-        const double s = bsum<NW>(vr[q], redd, tid);
-        if (tid == 0) part[l * rpb + q] = s;
-      }
+      if (tid < 32)
+        for (int q = 0; q < rpb; ++q) {
+          const double s = wsum(vr[q]);
+          if (tid == 0) part[l * rpb + q] = s;
+        }
       csync<NW>();
     }
     if (real) {
       // T = || L_S^dag K_0 ||_F^2, (L_S^dag K_0)[i][j] = sum_s conj(L_S[site_s][i]) K_0[site_s][j]
+      // (warp 0, fixed lane mapping)
       double tv = 0.0;
-      for (int o = tid; o < mS * mD; o += NT) {
-        const int i = o / mD, j = o - i * mD;
-        cx<T> acc = cz<T>();
-        for (int s = 0; s < mS; ++s) {
-          const int e = (i * s) % mS;
-          acc = cmac_cj(acc, tc<T>(mk(LS.tw[2 * e], LS.tw[2 * e + 1])), K[LS.sites[s] * mD + j]);
+      if (tid < 32)
+        for (int o = tid; o < mS * mD; o += 32) {
+          const int i = o / mD, j = o - i * mD;
+          cx<T> acc = cz<T>();
+          for (int s = 0; s < mS; ++s) {
+            const int e = (i * s) % mS;
+            acc = cmac_cj(acc, tc<T>(mk(LS.tw[2 * e], LS.tw[2 * e + 1])), K[LS.sites[s] * mD + j]);
+          }
+          tv += (double)abs2(acc) * sqS[i] * sqS[i];
         }
-        tv += (double)abs2(acc) * sqS[i] * sqS[i];
-      }
-      const double Tval = bsum<NW>(tv, redd, tid);
+      const double Tval = tid < 32 ? wsum(tv) : 0.0;
       if (tid == 0) a.Tpart[W.tout] = Tval;
       if (a.resid) {
         const double rn = cta_max<NW>(rnum, redd, tid);

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
     // ---------------- backward sweep
     cx<T> G = gl;             // G_{L-1,L-1}
     T c = abs2(G);            // |G_{l,L-1}|^2
-    // sum-rule residual of the lane: max_l |A_S + A_D + 2 Im G|_ll / max_l |2 Im G_ll|
+    // sum-rule residual of the lane: max(0, max_l (A_S + A_D + 2 Im G)_ll) / max_l |2 Im G_ll|
     double rnum = 0.0, rden = 0.0;
     for (int l = L - 1; l >= 0; --l) {
       const T* s = st + (long long)l * nf * 32;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
           // A_S + A_D + 2 Im G <= 0 up to rounding (equality up to 2 eta |G|^2 terms)
           const double as = gamS * (double)s[128 + lane] * (double)abs2(G);
           const double gim = (double)G.im;
-          rnum = fmax(rnum, fabs(as + gamD * (double)c + 2.0 * gim));
+          rnum = fmax(rnum, as + gamD * (double)c + 2.0 * gim);
           rden = fmax(rden, fabs(2.0 * gim));
         }
       } else {
@@ -355,8 +355,8 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
         v1 = wS * (double)abs2(P1) + wD * (double)abs2(K[1]);
         if (want_r) {
           const double g0 = (double)G.a[0][0].im, g1 = (double)G.a[1][1].im;
-          rnum = fmax(rnum, fabs((double)abs2(P0) + (double)abs2(K[0]) + 2.0 * g0));
-          rnum = fmax(rnum, fabs((double)abs2(P1) + (double)abs2(K[1]) + 2.0 * g1));
+          rnum = fmax(rnum, (double)abs2(P0) + (double)abs2(K[0]) + 2.0 * g0);
+          rnum = fmax(rnum, (double)abs2(P1) + (double)abs2(K[1]) + 2.0 * g1);
           rden = fmax(rden, fmax(fabs(2.0 * g0), fabs(2.0 * g1)));
         }
       } else {
