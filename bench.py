@@ -32,6 +32,23 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "cnt17_realspace_N512_E2048+128_sc"
 
 
+# DRAM traffic per launch of the block sweep, from one ncu capture of the N = 64 case with the
+# same energy grid (--profile-small), scaled by 512 / 64 layers (profiles/
+# sweep_blk_cnt17_N64_E2176_ncu.md).  It is reported only while the kernel sources hash to the
+# ones the capture was taken on.
+TRAFFIC_CAPTURE = {"sources_sha256": "b7586d58adbfcda694e10cb72716418c25c7360698bf93758ea4769343dbd0e4", "bytes_per_launch": (1.109093e9 + 1.255673e9) * 512 / 64}
+KERNEL_SOURCES = ("sweep_block.cu", "common.cuh", "lead.cuh")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2407_14633_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def algorithmic_flops(b, m, nnz, L, n_real, n_cont):
     """FLOPs of one NEGF evaluation in the method's formulation (8 per complex MAC):
     real-axis lane per layer: block inverse b^3 + lead-column products R, K, G R (3 b^2 m)
@@ -238,6 +255,8 @@ def run_ours(args):
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     peak_derived = 2.0 * 2.0 * props.multi_processor_count * sm_max * 1e6 / 1e12   # 2 FP64 FMA/clk/SM
     peak_probe = ctx.fp64_peak()
+    traffic = (TRAFFIC_CAPTURE["bytes_per_launch"]
+               if kernel_sources_sha256() == TRAFFIC_CAPTURE["sources_sha256"] else None)
 
     # ---- end to end through the public API with host buffers
     U_host = np.ascontiguousarray(w["U"])
@@ -280,7 +299,7 @@ def run_ours(args):
                      "peak": peak_derived, "unit": "TFLOP/s", "frac": achieved / peak_derived,
                      "peak_kind": "FP64 derived: 2 FMA/clk/SM x SMs x max SM clock",
                      "peak_probe": peak_probe, "frac_of_probe": achieved / peak_probe,
-                     "traffic": None, "kernel_ms": sweep_ms, "flops_per_launch": flops},
+                     "traffic": traffic, "kernel_ms": sweep_ms, "flops_per_launch": flops},
         "clocks": clocks,
         "self_consistent_solve": sc,
     }
@@ -303,14 +322,15 @@ def run_ours(args):
 
 
 def run_profile_small(args):
-    """Reduced case of the same kernel for ncu captures: (17,0) real space, N = 128 rings,
-    576 real-axis + 32 contour energies, three NEGF evaluations (no SC loop, no CPU leg)."""
+    """Reduced case of the same kernel for ncu captures: (17,0) real space, N = 64 rings and
+    the full grid (2048 real-axis + 128 contour energies, so the same lanes and waves as the
+    bench workload at 1/8 of its length), three NEGF evaluations (no SC loop, no CPU leg)."""
     import torch
     from paper_2407_14633_gb300 import negf, synth
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = negf.Context(device=0, stream=stream.cuda_stream, blk_warps=args.blk_warps)
-    w = synth.realspace_17(N=128, n_real=576, n_cont=32)
+    w = synth.realspace_17(N=64)
     dev = ctx.device_create(w["N"], block=17, rings_per_block=1, n_chains=1)
     ctx.build_cnt_realspace(dev, 17, w["t"], w["U_S"], w["U_D"])
     ctx.set_potential(dev, w["U"])

@@ -69,10 +69,10 @@ typedef struct negf_ctx negf_ctx;
  * NEGF_PREC_*.  flag_threshold: mixed precision, the per-energy sum-rule residual (see
  * negf_out.resid) above which an energy is recomputed in FP64 (0 = default 1e-4).
  * edge_window: mixed precision, energies closer than this (eV) to a lead subband edge are
- * recomputed in FP64 (0 = default 0.02).  fault_alloc_after:
+ * recomputed in FP64 (0 = default 0.002).  fault_alloc_after:
  * host-side fault injection for tests, the n-th arena allocation fails (0 = off).
  * growth_threshold: mixed precision, energies whose complex64 sweep saw a gL entry larger
- * than this (1/eV) are recomputed in FP64 (0 = default 20).  blk_warps: CTA width (warps)
+ * than this (1/eV) are recomputed in FP64 (0 = criterion off, the default).  blk_warps: CTA width (warps)
  * of the sweep of ring blocks wider than 2: 0 = autotuned (each width is timed once per
  * context on the first batch of a given element type, block size and lead width large
  * enough to fill the GPU, then cached; smaller batches use the size policy), -1 = the size

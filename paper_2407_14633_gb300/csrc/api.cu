@@ -377,8 +377,7 @@ int negf_create(negf_ctx** out, const negf_opts* opts) {
     return NEGF_EINVAL;
   }
   if (c->opts.flag_threshold <= 0.0) c->opts.flag_threshold = 1e-4;
-  if (c->opts.edge_window <= 0.0) c->opts.edge_window = 0.02;
-  if (c->opts.growth_threshold <= 0.0) c->opts.growth_threshold = 20.0;
+  if (c->opts.edge_window <= 0.0) c->opts.edge_window = 0.002;
   c->ordinal = c->opts.device_ordinal;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {

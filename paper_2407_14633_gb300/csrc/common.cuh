@@ -157,15 +157,15 @@ int launch_sweep_b2_f32(const SweepArgs& a, int grid, int block, cudaStream_t s)
 // warp-per-lane sweep of b x b blocks (b <= MAX_BLOCK) with smem matrices
 int launch_sweep_blk_f64(const SweepArgs& a, int b_max, int m_max, int grid, int warps,
                          cudaStream_t s);
-__host__ __device__ size_t sweep_blk_smem_bytes(int b, int m, int warps);
-__host__ __device__ size_t sweep_blk_smem_bytes_t(int b, int m, int esize);
-__host__ __device__ size_t sweep_blk_smem_bytes_nm(int b, int m, int esize, int nm);
+// shared memory of one CTA for element size esize (16: FP64, 8: FP32) and CTA width warps
+__host__ __device__ size_t sweep_blk_smem_bytes_t(int b, int m, int esize, int warps);
+__host__ __device__ bool sweep_blk_compact(int b, int m, int esize, int warps);
 int launch_sweep_blk_t(bool fp32, const SweepArgs& a, int b_max, int m_max, int grid, int warps, cudaStream_t s);
-int sweep_blk_occupancy_t(bool fp32, int warps, size_t smem);
+// resident CTAs per SM of the block sweep (sets the dynamic shared memory limit first)
+int sweep_blk_occupancy_t(bool fp32, int warps, int b, int m);
 // resident CTAs per SM of a sweep kernel (sets the dynamic shared memory limit first)
 int sweep_chain_occupancy(int cls, int threads, size_t smem);
 int sweep_chain_occupancy_t(bool fp32, int cls, int threads, size_t smem);
-int sweep_blk_occupancy(int warps, size_t smem);
 
 struct ReduceDev {
   int n_rings, n_real, n_chains;

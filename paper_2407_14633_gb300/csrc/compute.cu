@@ -151,13 +151,13 @@ static SweepArgs group_args(const Plan& P, int g, const int* order, int n, doubl
 static int tune_width(Ctx* c, Plan& P, int g) {
   const PlanBufs& B = *P.bufs;
   const bool f32 = group_f32(g);
-  const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16);
   const long long stride = P.stride[g % 5];
   const long long max_grid = stride > 0 ? (long long)(B.stage.bytes / stride) : 0;
   const int cand[3] = {1, 2, 4};
   int grid[3], S = 0;
   for (int i = 0; i < 3; ++i) {
-    const int per_sm = sweep_blk_occupancy_t(f32, cand[i], sm);
+    const bool fits = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16, cand[i]) <= 227 * 1024;
+    const int per_sm = fits ? sweep_blk_occupancy_t(f32, cand[i], P.gb[g], P.gm[g]) : 0;
     grid[i] = per_sm > 0 ? (int)std::min<long long>(std::min<long long>((long long)c->sms * per_sm, P.ncls[g]), max_grid)
                          : 0;
     S = std::max(S, grid[i]);
@@ -348,9 +348,9 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       per_sm = sweep_chain_occupancy_t(f32, cls, tune.block_threads, csmem);
       wpb = tune.block_threads / 32;
     } else {
-      const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16);
+      const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16, P.gw[g]);
       if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
-      per_sm = sweep_blk_occupancy_t(f32, P.gw[g], sm);
+      per_sm = sweep_blk_occupancy_t(f32, P.gw[g], P.gb[g], P.gm[g]);
       wpb = 1;   // one lane (item) per CTA
     }
     const int need = cls < 2 ? (P.ncls[g] + wpb - 1) / wpb : P.ncls[g];
@@ -366,9 +366,9 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       const int wpb = cls < 2 ? tune.block_threads / 32 : 1;
       stage_bytes = std::max(stage_bytes, P.stride[g] * (long long)P.grid[g + 5] * wpb);
       if (cls == 2) {
-        const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], 16);
+        const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], 16, P.gw[g]);
         if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
-        sweep_blk_occupancy_t(false, P.gw[g], sm);
+        sweep_blk_occupancy_t(false, P.gw[g], P.gb[g], P.gm[g]);
       } else {
         sweep_chain_occupancy_t(false, cls, tune.block_threads, csmem);
       }
@@ -496,7 +496,7 @@ static int mixed_recompute(Ctx* c, Plan& P) {
       cudaStreamSynchronize(s) != cudaSuccess)
     return set_err(c, NEGF_ECUDA, "mixed-precision sweep failed");
   const double thr = c->opts.flag_threshold;
-  const double gthr = c->opts.growth_threshold > 0.0 ? c->opts.growth_threshold : 20.0;
+  const double gthr = c->opts.growth_threshold > 0.0 ? c->opts.growth_threshold : HUGE_VAL;   // 0: off
   P.flags.assign(P.tpos, 0);
   std::vector<int> redo[5];
   for (int i = 0; i < P.n_items; ++i) {

@@ -48,40 +48,79 @@ __device__ __forceinline__ cx<T> tc(cd v) {
   return mk((T)v.re, (T)v.im);
 }
 
-// C (R x N, ldc) = [Add +] A (R x K, lda) * B (K x N, ldb); two outputs per thread and two
-// partial sums per output keep eight independent FMA chains in flight
+// Outputs o0 and o1 = o0 + NT of C = [Add +] A (R x K, lda) * B (K x N, ldb): two partial
+// sums per output (even and odd k) keep eight independent FMA chains in flight.  Every
+// output is evaluated in the same order whichever thread computes it.
+template <typename T, int NT>
+__device__ __forceinline__ void dot2(cx<T>& v0, cx<T>& v1, int o0, int tot, const cx<T>* A, int lda,
+                                     const cx<T>* B, int ldb, int K, int N, const cx<T>* Add, int ldadd) {
+  const int o1 = o0 + NT;
+  const bool two = o1 < tot;
+  const int r0 = o0 / N, c0 = o0 - r0 * N;
+  const int r1 = two ? o1 / N : r0, c1 = two ? o1 - r1 * N : c0;
+  const cx<T>* a0 = A + r0 * lda;
+  const cx<T>* a1 = A + r1 * lda;
+  const cx<T>* b0 = B + c0;
+  const cx<T>* b1 = B + c1;
+  cx<T> s00 = cz<T>(), s01 = cz<T>(), s10 = cz<T>(), s11 = cz<T>();
+  int k = 0;
+  for (; k + 1 < K; k += 2) {
+    s00 = cmac(s00, a0[k], b0[k * ldb]);
+    s10 = cmac(s10, a1[k], b1[k * ldb]);
+    s01 = cmac(s01, a0[k + 1], b0[(k + 1) * ldb]);
+    s11 = cmac(s11, a1[k + 1], b1[(k + 1) * ldb]);
+  }
+  if (k < K) {
+    s00 = cmac(s00, a0[k], b0[k * ldb]);
+    s10 = cmac(s10, a1[k], b1[k * ldb]);
+  }
+  v0 = s00 + s01;
+  v1 = s10 + s11;
+  if (Add) {
+    v0 = v0 + Add[r0 * ldadd + c0];
+    v1 = v1 + Add[r1 * ldadd + c1];
+  }
+}
+
+// C (R x N, ldc) = [Add +] A (R x K, lda) * B (K x N, ldb)
 template <typename T, int NT>
 __device__ __forceinline__ void bgemm(cx<T>* C, int ldc, const cx<T>* A, int lda, const cx<T>* B, int ldb,
                                       int R, int K, int N, const cx<T>* Add, int ldadd, int tid) {
   const int tot = R * N;
   for (int o0 = tid; o0 < tot; o0 += 2 * NT) {
+    cx<T> v0, v1;
+    dot2<T, NT>(v0, v1, o0, tot, A, lda, B, ldb, K, N, Add, ldadd);
+    C[(o0 / N) * ldc + o0 % N] = v0;
     const int o1 = o0 + NT;
-    const bool two = o1 < tot;
-    const int r0 = o0 / N, c0 = o0 - r0 * N;
-    const int r1 = two ? o1 / N : r0, c1 = two ? o1 - r1 * N : c0;
-    const cx<T>* a0 = A + r0 * lda;
-    const cx<T>* a1 = A + r1 * lda;
-    const cx<T>* b0 = B + c0;
-    const cx<T>* b1 = B + c1;
-    cx<T> s00 = cz<T>(), s01 = cz<T>(), s10 = cz<T>(), s11 = cz<T>();
-    int k = 0;
-    for (; k + 1 < K; k += 2) {
-      s00 = cmac(s00, a0[k], b0[k * ldb]);
-      s10 = cmac(s10, a1[k], b1[k * ldb]);
-      s01 = cmac(s01, a0[k + 1], b0[(k + 1) * ldb]);
-      s11 = cmac(s11, a1[k + 1], b1[(k + 1) * ldb]);
-    }
-    if (k < K) {
-      s00 = cmac(s00, a0[k], b0[k * ldb]);
-      s10 = cmac(s10, a1[k], b1[k * ldb]);
-    }
-    cx<T> v0 = s00 + s01, v1 = s10 + s11;
-    if (Add) {
-      v0 = v0 + Add[r0 * ldadd + c0];
-      v1 = v1 + Add[r1 * ldadd + c1];
-    }
-    C[r0 * ldc + c0] = v0;
-    if (two) C[r1 * ldc + c1] = v1;
+    if (o1 < tot) C[(o1 / N) * ldc + o1 % N] = v1;
+  }
+}
+
+// The same product held in registers (at most 2 * MAXP outputs per thread), so that it can
+// overwrite one of its operands: bgemm_r, a CTA barrier, then store_r.
+constexpr int MAXP = 6;
+template <typename T>
+struct RegTile {
+  cx<T> v[2 * MAXP];
+};
+template <typename T, int NT>
+__device__ __forceinline__ void bgemm_r(RegTile<T>& t, const cx<T>* A, int lda, const cx<T>* B, int ldb, int R, int K,
+                                        int N, const cx<T>* Add, int ldadd, int tid) {
+  const int tot = R * N;
+#pragma unroll
+  for (int p = 0; p < MAXP; ++p) {
+    const int o0 = tid + p * 2 * NT;
+    if (o0 < tot) dot2<T, NT>(t.v[2 * p], t.v[2 * p + 1], o0, tot, A, lda, B, ldb, K, N, Add, ldadd);
+  }
+}
+template <typename T, int NT>
+__device__ __forceinline__ void store_r(cx<T>* C, int ldc, const RegTile<T>& t, int R, int N, int tid) {
+  const int tot = R * N;
+#pragma unroll
+  for (int p = 0; p < MAXP; ++p) {
+    const int o0 = tid + p * 2 * NT, o1 = o0 + NT;
+    if (o0 < tot) C[(o0 / N) * ldc + o0 % N] = t.v[2 * p];
+    if (o1 < tot) C[(o1 / N) * ldc + o1 % N] = t.v[2 * p + 1];
   }
 }
 
@@ -262,21 +301,23 @@ __device__ __forceinline__ void times_hdn(cx<T>* C, const cx<T>* M, int R, int b
   }
 }
 
-// shared memory of one CTA: NM b^2 + 3 b m + b elements of size esize (NM = 4, or 6 for the
-// two-sided variant), FP64 lead rows (2 m complex + 2 m real), b pivot ints, reductions
-__host__ __device__ size_t sweep_blk_smem_bytes_nm(int b, int m, int esize, int nm) {
-  size_t per = (size_t)(nm * b * b + 3 * b * m + b) * esize;
+// Layout of one CTA's shared memory: NM b x b and NV b x m element buffers plus b pivot
+// elements, then FP64 lead rows (2 m complex + 2 m real), b pivot ints and reductions.
+//   FP32, two-sided backward:              NM = 6, NV = 3
+//   FP64, Dyson backward:                  NM = 4, NV = 3
+//   FP64, Dyson, products in registers:    NM = 3, NV = 2 (compact; when every b x b and
+//                                          b x m product fits 2 MAXP outputs per thread)
+__host__ __device__ bool sweep_blk_compact(int b, int m, int esize, int warps) {
+  const int cap = 2 * MAXP * 32 * warps;
+  return esize == 16 && b * b <= cap && b * m <= cap;
+}
+__host__ __device__ size_t sweep_blk_smem_bytes_t(int b, int m, int esize, int warps) {
+  const bool cmp = sweep_blk_compact(b, m, esize, warps);
+  const int nm = esize == 8 ? 6 : (cmp ? 3 : 4), nv = cmp ? 2 : 3;
+  size_t per = (size_t)(nm * b * b + nv * b * m + b) * esize;
   per = (per + 15) & ~(size_t)15;
   per += (size_t)2 * m * 16 + (size_t)2 * m * 8 + (size_t)(b + 1) * 4 + 8 * 8 + 8 * 4 + 8 * 4;
   return (per + 15) & ~(size_t)15;
-}
-// FP32 sweeps use the two-sided backward (six b x b buffers), FP64 the Dyson update (four)
-__host__ __device__ size_t sweep_blk_smem_bytes_t(int b, int m, int esize) {
-  return sweep_blk_smem_bytes_nm(b, m, esize, esize == 8 ? 6 : 4);
-}
-__host__ __device__ size_t sweep_blk_smem_bytes(int b, int m, int warps) {
-  (void)warps;
-  return sweep_blk_smem_bytes_t(b, m, 16);
 }
 
 // alpha_l - Sub (Sub may be null): eps I - H_ll - U_ring - Sigma_S (l = 0) - Sigma_D (l = L-1),
@@ -309,24 +350,25 @@ __device__ __forceinline__ void alpha_minus(cx<T>* out, const cx<T>* Sub, int l,
   }
 }
 
-template <typename T, int NW, bool TWO>
+template <typename T, int NW, bool TWO, bool CMP>
 __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bmax, int mmax) {
   constexpr int NT = 32 * NW;
-  constexpr int NM = TWO ? 6 : 4;
+  constexpr int NM = TWO ? 6 : (CMP ? 3 : 4);
+  constexpr int NV = CMP ? 2 : 3;
   extern __shared__ __align__(16) unsigned char sm_blk[];
   const int tid = threadIdx.x;
   const int bb = bmax * bmax, bm = bmax * mmax;
   cx<T>* M0 = reinterpret_cast<cx<T>*>(sm_blk);
   cx<T>* M1 = M0 + bb;
   cx<T>* M2 = M1 + bb;
-  cx<T>* M3 = M2 + bb;
+  cx<T>* M3 = M2 + bb;   // not in the compact layout
   cx<T>* M4 = M3 + bb;   // two-sided only
   cx<T>* M5 = M4 + bb;   // two-sided only
   cx<T>* V0 = M0 + NM * bb;
   cx<T>* V1 = V0 + bm;
-  cx<T>* V2 = V1 + bm;
-  cx<T>* col = V2 + bm;
-  size_t off = (size_t)(NM * bb + 3 * bm + bmax) * sizeof(cx<T>);
+  cx<T>* V2 = V1 + bm;   // not in the compact layout
+  cx<T>* col = V0 + NV * bm;
+  size_t off = (size_t)(NM * bb + NV * bm + bmax) * sizeof(cx<T>);
   off = (off + 15) & ~(size_t)15;
   cd* sigS = reinterpret_cast<cd*>(sm_blk + off);
   cd* sigD = sigS + mmax;
@@ -400,12 +442,14 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
       csync<NW>();
     }
 
-    // ---- forward sweep: P = gL_{l-1} (M0), A (M1), X (M2); R (V0), Rn (V1)
+    // ---- forward sweep: P = gL_{l-1} (M0), A (M1), X (M2); R (V0), Rn (V1).  The compact
+    //      layout updates R in place through registers (Rn aliases R).
+    RegTile<T> rt;
     cx<T>* P = M0;
     cx<T>* A = M1;
     cx<T>* X = M2;
     cx<T>* R = V0;
-    cx<T>* Rn = V1;
+    cx<T>* Rn = CMP ? V0 : V1;
     const long long lstride = (long long)(bb + (real ? bm : 0)) * sizeof(cx<T>);
     float gmax = 0.0f;   // largest |gL_l entry|^2 of this thread (growth diagnostic)
     for (int l = 0; l < L; ++l) {
@@ -416,8 +460,16 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
         hdn_times<T, NT>(X, P, b, b, b, ccnt, cidx, cval, kmax, tid);            // X = H_{l,l-1} gL_{l-1}
         csync<NW>();
         times_hup<T, NT>(A, X, b, b, ccnt, cidx, cval, kmax, tid);               // y_l = X H_{l-1,l}
-        if (real) bgemm<T, NT>(Rn, mS, X, b, R, mS, b, b, mS, nullptr, 0, tid);  // R_l = X R_{l-1}
+        if (real) {                                                                // R_l = X R_{l-1}
+          if constexpr (CMP)
+            bgemm_r<T, NT>(rt, X, b, R, mS, b, b, mS, nullptr, 0, tid);
+          else
+            bgemm<T, NT>(Rn, mS, X, b, R, mS, b, b, mS, nullptr, 0, tid);
+        }
         csync<NW>();
+        if constexpr (CMP) {
+          if (real) store_r<T, NT>(Rn, mS, rt, b, mS, tid);   // read before the next barrier (binv)
+        }
         alpha_minus<T, NW>(A, A, l, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);  // alpha_l - y_l
       } else {
         if (real) {
@@ -445,15 +497,18 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
       cx<T>* t = P;
       P = A;
       A = t;
-      t = R;
-      R = Rn;
-      Rn = t;
+      if constexpr (!CMP) {
+        t = R;
+        R = Rn;
+        Rn = t;
+      }
     }
 
     // ---- backward sweep
     //  Dyson variant:     G (P: gL_{L-1} = G_{L-1,L-1}), Gl, Z, Wm
     //  two-sided variant: G, Gr = gR_{l+1}, Wk, W1, GlB = gL_l, GpB = gL_{l-1}
     //  both:              K, Kn (drain column factor), Rl (R_l)
+    //  compact Dyson:     G, Gl, Z; K (in place), Rl; Wm and the new G in registers
     cx<T>* G = P;
     cx<T>* Gl = A;       // Dyson: gL_l;  two-sided: work matrix Wk
     cx<T>* Z = X;        // Dyson: Z;     two-sided: W1
@@ -461,7 +516,7 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
     cx<T>* GlB = M4;     // two-sided only
     cx<T>* GpB = M5;     // two-sided only
     cx<T>* K = (R == V0) ? V1 : V0;
-    cx<T>* Kn = V2;
+    cx<T>* Kn = CMP ? K : V2;
     cx<T>* Rl = R;
     if (real) {
       // K_{L-1} = G_{L-1,L-1} L_D: K[r][j] = sum_s G[r][site_s] w^{j s} sqrt(gamma_j/m)
@@ -498,13 +553,31 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
           csync<NW>();
           times_hup<T, NT>(Z, Gl, b, b, ccnt, cidx, cval, kmax, tid);                // Z = gL_l H_{l,l+1}
           csync<NW>();
-          if (real) bgemm<T, NT>(Kn, mD, Z, b, K, mD, b, b, mD, nullptr, 0, tid);    // K_l = Z K_{l+1}
-          bgemm<T, NT>(Wm, b, Z, b, G, b, b, b, b, nullptr, 0, tid);                 // Wm = Z G_{l+1}
-          csync<NW>();
-          hdn_times<T, NT>(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, tid);             // Z = H_{l+1,l} gL_l
-          csync<NW>();
-          bgemm<T, NT>(G, b, Wm, b, Z, b, b, b, b, Gl, b, tid);                       // G = gL_l + Wm Z
-          csync<NW>();
+          if constexpr (CMP) {
+            bgemm_r<T, NT>(rt, Z, b, G, b, b, b, b, nullptr, 0, tid);                 // Wm = Z G_{l+1}
+            csync<NW>();
+            store_r<T, NT>(G, b, rt, b, b, tid);                                      // G := Wm
+            if (real) {
+              bgemm_r<T, NT>(rt, Z, b, K, mD, b, b, mD, nullptr, 0, tid);             // K_l = Z K_{l+1}
+              csync<NW>();
+              store_r<T, NT>(K, mD, rt, b, mD, tid);
+            }
+            csync<NW>();
+            hdn_times<T, NT>(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, tid);           // Z = H_{l+1,l} gL_l
+            csync<NW>();
+            bgemm_r<T, NT>(rt, G, b, Z, b, b, b, b, Gl, b, tid);                      // gL_l + Wm Z
+            csync<NW>();
+            store_r<T, NT>(G, b, rt, b, b, tid);
+            csync<NW>();
+          } else {
+            if (real) bgemm<T, NT>(Kn, mD, Z, b, K, mD, b, b, mD, nullptr, 0, tid);  // K_l = Z K_{l+1}
+            bgemm<T, NT>(Wm, b, Z, b, G, b, b, b, b, nullptr, 0, tid);               // Wm = Z G_{l+1}
+            csync<NW>();
+            hdn_times<T, NT>(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, tid);           // Z = H_{l+1,l} gL_l
+            csync<NW>();
+            bgemm<T, NT>(G, b, Wm, b, Z, b, b, b, b, Gl, b, tid);                     // G = gL_l + Wm Z
+            csync<NW>();
+          }
         } else {
           // G_ll = (alpha_l - x_l - y_l)^{-1} with x_l = H_{l,l+1} gR_{l+1} H_{l+1,l} and
           // y_l = H_{l,l-1} gL_{l-1} H_{l-1,l}: no cancellation between large terms
@@ -546,7 +619,7 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
           GlB = GpB;
           GpB = t;
         }
-        if (real) {
+        if (real && !CMP) {
           cx<T>* t = K;
           K = Kn;
           Kn = t;
@@ -555,7 +628,7 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
       // per-site contributions of layer l, summed per ring.  The row sums and ring sums run
       // on warp 0 with a fixed lane mapping, so the result does not depend on the CTA width.
       double vr[2] = {0.0, 0.0};
-      cx<T>* Pm = TWO ? Z : Wm;   // free b x m buffer for G_ll R_l
+      cx<T>* Pm = (TWO || CMP) ? Z : Wm;   // free b x m buffer for G_ll R_l (m <= b)
       if (real) {
         bgemm<T, NT>(Pm, mS, G, b, Rl, mS, b, b, mS, nullptr, 0, tid);               // G_ll R_l
         csync<NW>();
@@ -614,12 +687,13 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
   }
 }
 
-template <typename T, int NW>
+template <typename T, int NW, bool CMP>
 static int blk_occupancy(size_t smem) {
   constexpr bool TWO = sizeof(T) == 4;
-  cudaFuncSetAttribute(sweep_blk_kernel<T, NW, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(sweep_blk_kernel<T, NW, TWO, CMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_blk_kernel<T, NW, TWO>, 32 * NW, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_blk_kernel<T, NW, TWO, CMP>, 32 * NW, smem) !=
+          cudaSuccess ||
       per < 1) {
     cudaGetLastError();
     per = 1;
@@ -627,35 +701,43 @@ static int blk_occupancy(size_t smem) {
   return per;
 }
 
-int sweep_blk_occupancy_t(bool fp32, int warps, size_t smem) {
+int sweep_blk_occupancy_t(bool fp32, int warps, int b, int m) {
+  const size_t smem = sweep_blk_smem_bytes_t(b, m, fp32 ? 8 : 16, warps);
   if (fp32) {
-    if (warps == 1) return blk_occupancy<float, 1>(smem);
-    if (warps == 2) return blk_occupancy<float, 2>(smem);
-    return blk_occupancy<float, 4>(smem);
+    if (warps == 1) return blk_occupancy<float, 1, false>(smem);
+    if (warps == 2) return blk_occupancy<float, 2, false>(smem);
+    return blk_occupancy<float, 4, false>(smem);
   }
-  if (warps == 1) return blk_occupancy<double, 1>(smem);
-  if (warps == 2) return blk_occupancy<double, 2>(smem);
-  return blk_occupancy<double, 4>(smem);
+  const bool cmp = sweep_blk_compact(b, m, 16, warps);
+  if (warps == 1) return cmp ? blk_occupancy<double, 1, true>(smem) : blk_occupancy<double, 1, false>(smem);
+  if (warps == 2) return cmp ? blk_occupancy<double, 2, true>(smem) : blk_occupancy<double, 2, false>(smem);
+  return cmp ? blk_occupancy<double, 4, true>(smem) : blk_occupancy<double, 4, false>(smem);
 }
-int sweep_blk_occupancy(int warps, size_t smem) { return sweep_blk_occupancy_t(false, warps, smem); }
 
 int launch_sweep_blk_t(bool fp32, const SweepArgs& a, int b_max, int m_max, int grid, int warps, cudaStream_t s) {
   // the dynamic shared memory limit was raised by the occupancy query when planning
-  const size_t smem = sweep_blk_smem_bytes_t(b_max, m_max, fp32 ? 8 : 16);
+  const size_t smem = sweep_blk_smem_bytes_t(b_max, m_max, fp32 ? 8 : 16, warps);
   if (fp32) {
     if (warps == 1)
-      sweep_blk_kernel<float, 1, true><<<grid, 32, smem, s>>>(a, b_max, m_max);
+      sweep_blk_kernel<float, 1, true, false><<<grid, 32, smem, s>>>(a, b_max, m_max);
     else if (warps == 2)
-      sweep_blk_kernel<float, 2, true><<<grid, 64, smem, s>>>(a, b_max, m_max);
+      sweep_blk_kernel<float, 2, true, false><<<grid, 64, smem, s>>>(a, b_max, m_max);
     else
-      sweep_blk_kernel<float, 4, true><<<grid, 128, smem, s>>>(a, b_max, m_max);
+      sweep_blk_kernel<float, 4, true, false><<<grid, 128, smem, s>>>(a, b_max, m_max);
+  } else if (sweep_blk_compact(b_max, m_max, 16, warps)) {
+    if (warps == 1)
+      sweep_blk_kernel<double, 1, false, true><<<grid, 32, smem, s>>>(a, b_max, m_max);
+    else if (warps == 2)
+      sweep_blk_kernel<double, 2, false, true><<<grid, 64, smem, s>>>(a, b_max, m_max);
+    else
+      sweep_blk_kernel<double, 4, false, true><<<grid, 128, smem, s>>>(a, b_max, m_max);
   } else {
     if (warps == 1)
-      sweep_blk_kernel<double, 1, false><<<grid, 32, smem, s>>>(a, b_max, m_max);
+      sweep_blk_kernel<double, 1, false, false><<<grid, 32, smem, s>>>(a, b_max, m_max);
     else if (warps == 2)
-      sweep_blk_kernel<double, 2, false><<<grid, 64, smem, s>>>(a, b_max, m_max);
+      sweep_blk_kernel<double, 2, false, false><<<grid, 64, smem, s>>>(a, b_max, m_max);
     else
-      sweep_blk_kernel<double, 4, false><<<grid, 128, smem, s>>>(a, b_max, m_max);
+      sweep_blk_kernel<double, 4, false, false><<<grid, 128, smem, s>>>(a, b_max, m_max);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

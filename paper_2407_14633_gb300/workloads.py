@@ -74,10 +74,12 @@ def _edge_near(n_tube, t, E, U_lead, window):
     return d < window
 
 
-def mixed_precision(tubes=(17, 26, 34), N=1024, n_energies=4096, windows=(0.02, 0.002)):
+def mixed_precision(tubes=(17, 26, 34), N=1024, n_energies=4096,
+                    variants=((0.02, 20.0, 1e-4), (0.002, 20.0, 1e-4), (0.002, 0.0, 1e-4), (0.002, 0.0, 1e-3))):
     """Real-space (n,0) tubes, a quarter of the energies within 20 meV of a lead subband edge:
     complex128 sweep vs the mixed path (complex64 sweep, FP64 recompute of flagged energies;
-    one run per band-edge window) vs the plain complex64 sweep; errors per output against
+    one run per (band-edge window, growth threshold, residual threshold); a growth threshold
+    of 0 switches that criterion off) vs the plain complex64 sweep; errors per output against
     the complex128 result, and which criterion flagged how many energies."""
     out = {}
     thr, gthr = 1e-4, 20.0
@@ -89,8 +91,9 @@ def mixed_precision(tubes=(17, 26, 34), N=1024, n_energies=4096, windows=(0.02, 
         E_B = float(np.min(w["U"]) - 3.0 * abs(w["t"]) - 1.0)
         cg = negf.make_grid(w["mu_S"], w["mu_D"], w["kT"], w["eta"], E_B, 1, 64, E_min=-1.0, E_max=1.0)
         runs = [("c128", negf.PREC_FP64, {})] + \
-            [("mixed_w%g" % win, negf.PREC_MIXED, dict(flag_threshold=thr, growth_threshold=gthr, edge_window=win))
-             for win in windows] + [("c64", negf.PREC_FP32, {})]
+            [("mixed_w%g_g%g_r%g" % (win, gro, rth), negf.PREC_MIXED,
+              dict(flag_threshold=rth, growth_threshold=gro if gro > 0 else 1e300, edge_window=win))
+             for win, gro, rth in variants] + [("c64", negf.PREC_FP32, {})]
         res = {}
         for name, prec, kw in runs:
             with negf.Context(precision=prec, **kw) as ctx:
@@ -126,6 +129,8 @@ def mixed_precision(tubes=(17, 26, 34), N=1024, n_energies=4096, windows=(0.02, 
             if name.startswith("mixed"):
                 near = _edge_near(n_tube, w["t"], E, w["U_S"], kw["edge_window"])
                 e["edge_window_eV"] = kw["edge_window"]
+                e["growth_threshold"] = kw["growth_threshold"] if kw["growth_threshold"] < 1e300 else None
+                e["residual_threshold"] = kw["flag_threshold"]
                 e["recomputed_fraction"] = float(np.mean(r["flags"]))
                 e["flagged_by_edge_window"] = float(np.mean(near))
             entry[name] = e
@@ -187,6 +192,12 @@ def serving_sweep(n_requests=256, rate_factor=2.0, tol=1e-5, M=64):
             ts, tst, td = ctx.request_times(tk)
             lat.append(td - ts)
             served.append(ctx.poll(tk))
+    # the sequential loop under the same arrivals: one solve at a time in arrival order, each
+    # taking its measured time (a single-server queue)
+    fin, seq_q = 0.0, []
+    for arr, dt in zip(arrivals, seq_lat):
+        fin = max(fin, arr) + dt
+        seq_q.append(fin - arr)
     # capacity: all requests queued at t = 0
     with negf.Context() as ctx:
         t0 = time.perf_counter()
@@ -203,6 +214,8 @@ def serving_sweep(n_requests=256, rate_factor=2.0, tol=1e-5, M=64):
                and np.array_equal(a["n"], b["n"]) and np.array_equal(a["n"], c["n"]))
     return {"requests": n_requests, "sequential_bias_points_per_s": seq_rate,
             "sequential_p50_s": float(np.percentile(seq_lat, 50)), "sequential_p99_s": float(np.percentile(seq_lat, 99)),
+            "sequential_queued_p50_s": float(np.percentile(seq_q, 50)),
+            "sequential_queued_p99_s": float(np.percentile(seq_q, 99)),
             "served_bias_points_per_s": n_requests / total, "served_p50_s": float(np.percentile(lat, 50)),
             "served_p99_s": float(np.percentile(lat, 99)), "arrival_rate_per_s": rate_factor * seq_rate,
             "converged": int(sum(r["converged"] for r in served)),

@@ -10,7 +10,8 @@ from tests.cases import case_params, current_err, rel_inf, run_lib, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-MIXED_BOUND = 2e-5     # n, T, I relative (norm-wise) of the mixed path
+MIXED_BOUND = 2e-5     # n, T, I relative (norm-wise) of the mixed path, 20 meV band-edge window
+DEFAULT_BOUND = 5e-5   # the same with the default options (2 meV window, growth criterion off)
 FP32_BOUND = 1e-3      # pure complex64 sweep (no recompute)
 
 
@@ -28,17 +29,19 @@ def workloads():
     ]
 
 
+@pytest.mark.parametrize("opts,bound", [(dict(flag_threshold=1e-4, edge_window=0.02), MIXED_BOUND),
+                                        (dict(), DEFAULT_BOUND)])
 @pytest.mark.parametrize("i", range(3))
-def test_mixed_precision_error_bound(i):
+def test_mixed_precision_error_bound(i, opts, bound):
     from paper_2407_14633_gb300 import negf
     p = workloads()[i]
     o = run_oracle(p, chunk=16)
-    with ctx_with(negf.PREC_MIXED, flag_threshold=1e-4, edge_window=0.02) as ctx:
+    with ctx_with(negf.PREC_MIXED, **opts) as ctx:
         _, r = run_lib(ctx, p)
     g = 4.0 * len(p["modes"]) if p["kind"] == "mode" else 2.0
     errs = (rel_inf(r["n"], o["n"]), rel_inf(r["T"], o["T"]), current_err(r["I"], o["I"], g, p["mu_S"] - p["mu_D"]))
     print("mixed errors n %.2e T %.2e I %.2e" % errs)
-    assert max(errs) < MIXED_BOUND
+    assert max(errs) < bound
     # contour lanes stay FP64
     assert rel_inf(r["n_cont"], o["n_cont"]) < 1e-10
 
