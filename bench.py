@@ -36,7 +36,8 @@ WORKLOAD = "cnt17_realspace_N512_E2048+128_sc"
 # same energy grid (--profile-small), scaled by 512 / 64 layers (profiles/
 # sweep_blk_cnt17_N64_E2176_ncu.md).  It is reported only while the kernel sources hash to the
 # ones the capture was taken on.
-TRAFFIC_CAPTURE = {"sources_sha256": "b7586d58adbfcda694e10cb72716418c25c7360698bf93758ea4769343dbd0e4", "bytes_per_launch": (1.109093e9 + 1.255673e9) * 512 / 64}
+TRAFFIC_CAPTURE = {"sources_sha256": "ffed9d1d9d40b8c32316944d7488943cad946c3b439ef9194637f0677bb2ac00",
+                   "bytes_per_launch": (1.115161e9 + 1.255502e9) * 512 / 64}
 KERNEL_SOURCES = ("sweep_block.cu", "common.cuh", "lead.cuh")
 
 
@@ -49,13 +50,18 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def algorithmic_flops(b, m, nnz, L, n_real, n_cont):
-    """FLOPs of one NEGF evaluation in the method's formulation (8 per complex MAC):
-    real-axis lane per layer: block inverse b^3 + lead-column products R, K, G R (3 b^2 m)
-    + two dense products of the G_ll update (2 b^3) + four coupling products (4 b^2 nnz);
-    contour lane per layer: inverse + G_ll update (3 b^3) + four coupling products."""
-    real = 3 * b ** 3 + 3 * b * b * m + 4 * b * b * nnz
-    cont = 3 * b ** 3 + 4 * b * b * nnz
+def algorithmic_flops(b, m, nnz, L, n_real, n_cont, sym=True):
+    """FLOPs of one NEGF evaluation as the block sweep computes it (8 per complex MAC).
+    Per layer, real-axis lane: block inverse b^3, lead-column products R, K, G R (3 b^2 m),
+    the G_ll update Z G_{l+1} (b^3) then (Z G_{l+1}) Z^T + gL_l, and the sparse coupling
+    products.  For a chain with complex symmetric Green's functions (sym: real H blocks and
+    real lead rows, as for the nanotube) the second product is the upper triangle only,
+    b^2 (b + 1) / 2, and three coupling products (3 b^2 nnz) remain; otherwise b^3 and four.
+    Contour lane: the same without the lead-column products."""
+    upd = b ** 3 + (b * b * (b + 1) // 2 if sym else b ** 3)
+    sparse = (3 if sym else 4) * b * b * nnz
+    real = b ** 3 + upd + 3 * b * b * m + sparse
+    cont = b ** 3 + upd + sparse
     return 8.0 * L * (n_real * real + n_cont * cont)
 
 
@@ -291,7 +297,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "n_rings": N, "block": 17, "energies_real": n_real,
                    "energies_contour": n_cont, "step": "one self-consistent iteration (captured graph)",
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas per rank (weak)",
-                   "cta_warps": ctx.blk_width(17, 17)},
+                   "launch_shape": ctx.blk_shape(17, 17)},
         "e2e": {"value": units_per_step / t_e2e, "unit": "ring-energy updates/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "call": "negf_set_potential + negf_compute, host buffers"},
         "gpu_launches": int(launches),
@@ -329,7 +335,8 @@ def run_profile_small(args):
     from paper_2407_14633_gb300 import negf, synth
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    ctx = negf.Context(device=0, stream=stream.cuda_stream, blk_warps=args.blk_warps)
+    ctx = negf.Context(device=0, stream=stream.cuda_stream, blk_warps=args.blk_warps,
+                       blk_ctas_per_sm=args.blk_ctas)
     w = synth.realspace_17(N=64)
     dev = ctx.device_create(w["N"], block=17, rings_per_block=1, n_chains=1)
     ctx.build_cnt_realspace(dev, 17, w["t"], w["U_S"], w["U_D"])
@@ -341,7 +348,7 @@ def run_profile_small(args):
     ms, k = ctx.kernel_time()
     flops = algorithmic_flops(17, 17, 1.5, w["N"], w["n_real"], w["n_cont"])
     print(json.dumps({"case": "profile_small", "sweep_ms": ms / k, "tflops": flops / (ms / k * 1e-3) / 1e12,
-                      "I": r["I"], "cta_warps": args.blk_warps}))
+                      "I": r["I"], "cta_warps": args.blk_warps, "ctas_per_sm": args.blk_ctas}))
     ctx.close()
     return 0
 
@@ -361,6 +368,8 @@ def main():
                     help="reduced case of the block sweep for ncu captures")
     ap.add_argument("--blk-warps", type=int, default=1,
                     help="CTA width of the block sweep in --profile-small (no tuning launches)")
+    ap.add_argument("--blk-ctas", type=int, default=0,
+                    help="cap on resident CTAs per SM of the block sweep in --profile-small (0: no cap)")
     args = ap.parse_args()
     if args.profile_small:
         return run_profile_small(args)

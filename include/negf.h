@@ -74,10 +74,11 @@ typedef struct negf_ctx negf_ctx;
  * growth_threshold: mixed precision, energies whose complex64 sweep saw a gL entry larger
  * than this (1/eV) are recomputed in FP64 (0 = criterion off, the default).  blk_warps: CTA width (warps)
  * of the sweep of ring blocks wider than 2: 0 = autotuned (each width is timed once per
- * context on the first batch of a given element type, block size and lead width large
- * enough to fill the GPU, then cached; smaller batches use the size policy), -1 = the size
- * policy (1 warp up to b = 20, 2 up to 28, else 4), 1 / 2 / 4 = that width.  Results are
- * bitwise the same for every width. */
+ * context, with the resident CTAs per SM, on the first batch of a given element type,
+ * block size, lead width and item count that has at least one item per SM, then cached;
+ * smaller batches use the size policy), -1 = the size policy (1 warp up to b = 20, 2 up to
+ * 28, else 4), 1 / 2 / 4 = that width.  Results are bitwise the same for every width.  blk_ctas_per_sm: cap on the resident CTAs per SM of
+ * that sweep (0 = as many as fit); the grid is the cap times the SMs. */
 typedef struct {
   int device_ordinal;
   void* stream;
@@ -88,6 +89,7 @@ typedef struct {
   int fault_alloc_after;
   double growth_threshold;
   int blk_warps;
+  int blk_ctas_per_sm;
 } negf_opts;
 
 /* Create / destroy a context on one GPU.  opts may be NULL (defaults: device 0, own
@@ -377,9 +379,10 @@ int negf_launch_count(const negf_ctx* ctx, uint64_t* launches);
 int negf_profile(negf_ctx* ctx, int enable);
 int negf_kernel_time(negf_ctx* ctx, double* sweep_ms, uint64_t* sweeps);
 
-/* The CTA width (warps) the autotuner chose for ring blocks of width b with leads of m
- * sites in FP64 (fp32 = 0) or FP32 (fp32 = 1); NEGF_EINVAL if that shape was not tuned. */
-int negf_blk_width(negf_ctx* ctx, int fp32, int b, int m, int* warps);
+/* The launch shape the autotuner last chose for ring blocks of width b with leads of m
+ * sites in FP64 (fp32 = 0) or FP32 (fp32 = 1): CTA width in warps and resident CTAs per SM
+ * (ctas_per_sm may be NULL); NEGF_EINVAL if that shape was not tuned. */
+int negf_blk_width(negf_ctx* ctx, int fp32, int b, int m, int* warps, int* ctas_per_sm);
 
 /* Measured FP64 FMA throughput of this GPU (TFLOP/s): a register-resident FMA loop over
  * every SM, best of three, for the FP64 roofline of the sweep kernels. */

@@ -137,6 +137,19 @@ int upload_lead(Ctx* c, ChainData& ch, int side) {
 int upload_chain(Ctx* c, Dev* d, ChainData& ch) {
   const int b = d->block, L = d->L;
   int rc;
+  ch.h_sym = true;
+  for (int l = 0; l < L && ch.h_sym; ++l)
+    for (int r = 0; r < b && ch.h_sym; ++r)
+      for (int q = 0; q < b; ++q) {
+        const double* v = &ch.Hdiag[2 * ((size_t)l * b * b + (size_t)r * b + q)];
+        const double* w = &ch.Hdiag[2 * ((size_t)l * b * b + (size_t)q * b + r)];
+        if (v[1] != 0.0 || v[0] != w[0]) {
+          ch.h_sym = false;
+          break;
+        }
+      }
+  for (size_t i = 1; i < ch.Hup.size() && ch.h_sym; i += 2)
+    if (ch.Hup[i] != 0.0) ch.h_sym = false;
   if ((rc = upload(c, ch.dHdiag, ch.Hdiag.data(), ch.Hdiag.size() * 8))) return rc;
   if ((rc = upload(c, ch.dHup, ch.Hup.data(), std::max<size_t>(ch.Hup.size(), 2) * 8))) return rc;
   int kmax = 1;
@@ -372,7 +385,8 @@ int negf_create(negf_ctx** out, const negf_opts* opts) {
   if (!c) return NEGF_ENOMEM;
   if (opts) c->opts = *opts;
   const int bw = c->opts.blk_warps;
-  if (c->opts.precision < 0 || c->opts.precision > 2 || !(bw == -1 || bw == 0 || bw == 1 || bw == 2 || bw == 4)) {
+  if (c->opts.precision < 0 || c->opts.precision > 2 || !(bw == -1 || bw == 0 || bw == 1 || bw == 2 || bw == 4) ||
+      c->opts.blk_ctas_per_sm < 0) {
     delete c;
     return NEGF_EINVAL;
   }

@@ -53,6 +53,15 @@ __host__ __device__ __forceinline__ cx<T> cmac_cj(cx<T> acc, cx<T> a, cx<T> b) {
   acc.im = fma(-a.im, b.re, acc.im);
   return acc;
 }
+// acc - a * b (the negation folds into the multiply-adds)
+template <typename T>
+__host__ __device__ __forceinline__ cx<T> cmsub(cx<T> acc, cx<T> a, cx<T> b) {
+  acc.re = fma(-a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
 // 1 / a = conj(a) / |a|^2
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> crecip(cx<T> a) {
@@ -99,6 +108,7 @@ struct ChainView {
   int kmax;
   const double* hsq; // block 1: |H_{l,l+1}|^2 per layer (L-1)
   double g_b;
+  int sym;           // real H blocks and real lead rows: every G_ll is complex symmetric
   LeadView lead[2];
 };
 

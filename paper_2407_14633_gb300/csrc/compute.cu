@@ -75,6 +75,13 @@ DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
     cv.kmax = ch.kmax;
     cv.hsq = (const double*)ch.dhsq.p;
     cv.g_b = ch.g_b;
+    // complex symmetric Green's functions: real symmetric H blocks, real couplings and leads
+    // whose circulant couplings have real first rows (their Sigma is then symmetric)
+    bool lead_real = true;
+    for (int s2 = 0; s2 < 2; ++s2)
+      for (const std::vector<double>* f : {&ch.lead[s2].T1, &ch.lead[s2].T2, &ch.lead[s2].tau})
+        for (size_t i = 1; i < f->size(); i += 2) lead_real = lead_real && (*f)[i] == 0.0;
+    cv.sym = (ch.h_sym && lead_real) ? 1 : 0;
     for (int s = 0; s < 2; ++s) {
       LeadView& lv = cv.lead[s];
       lv.m = ch.lead[s].m;
@@ -122,8 +129,6 @@ static int group_of(int cls, int b, bool f32) {
 static int group_class(int g) { return std::min(g % 5, 2); }
 static bool group_f32(int g) { return g >= 5; }
 
-static long long width_key(bool f32, int b, int m) { return ((long long)f32 << 40) | ((long long)b << 20) | m; }
-
 static SweepArgs group_args(const Plan& P, int g, const int* order, int n, double* resid, double* growth) {
   const PlanBufs& B = *P.bufs;
   SweepArgs a;
@@ -142,58 +147,98 @@ static SweepArgs group_args(const Plan& P, int g, const int* order, int n, doubl
   return a;
 }
 
-// Autotuner of the CTA width of the wide-block sweep.  Every output element and every
-// reduction of that kernel has an evaluation order that does not depend on the width, so
-// the choice changes speed only.  Each candidate width (1, 2, 4 warps) runs the same first
-// items of the group, one full wave of the candidate with the most resident CTAs, once to
-// warm up and once timed with events; the fastest is cached per (element type, b, m).  The
-// trial outputs are overwritten by the real launch.
+// Resident CTAs per SM of the wide-block sweep for n items on sms SMs when at most occ fit:
+// the largest cap whose last wave is empty or at least half full.  A thin last wave leaves
+// most SMs with one or two lanes, too few to keep the FP64 pipe busy.
+static int cap_rule(long long n, int sms, int occ) {
+  const double L = (double)n / sms;
+  for (int cap = occ; cap > (occ + 1) / 2; --cap) {
+    const double q = L - std::floor(L / cap) * cap;
+    if (q < 1e-9 || q >= 0.5 * cap) return cap;
+  }
+  return occ;
+}
+
+static int blk_occ(Ctx* c, bool f32, int w, int b, int m) {
+  if (sweep_blk_smem_bytes_t(b, m, f32 ? 8 : 16, w) > 227 * 1024) return 0;
+  int occ = sweep_blk_occupancy_t(f32, w, b, m);
+  if (c->opts.blk_ctas_per_sm > 0) occ = std::min(occ, c->opts.blk_ctas_per_sm);
+  return occ;
+}
+
+// Autotuner of the wide-block sweep's launch shape: CTA width (1, 2, 4 warps) and resident
+// CTAs per SM.  Every output element and every reduction of that kernel has an evaluation
+// order that depends on neither, so the choice changes speed only.  The candidates are, per
+// width, the occupancy limit and the cap of cap_rule; each runs the whole group (so that the
+// last wave is measured too) after one single-item launch per width has loaded the kernel.
+// The fastest is cached per (element type, b, m, items); trial outputs are overwritten by the
+// real launch.
 static int tune_width(Ctx* c, Plan& P, int g) {
   const PlanBufs& B = *P.bufs;
   const bool f32 = group_f32(g);
+  const int n = P.ncls[g];
   const long long stride = P.stride[g % 5];
   const long long max_grid = stride > 0 ? (long long)(B.stage.bytes / stride) : 0;
-  const int cand[3] = {1, 2, 4};
-  int grid[3], S = 0;
-  for (int i = 0; i < 3; ++i) {
-    const bool fits = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16, cand[i]) <= 227 * 1024;
-    const int per_sm = fits ? sweep_blk_occupancy_t(f32, cand[i], P.gb[g], P.gm[g]) : 0;
-    grid[i] = per_sm > 0 ? (int)std::min<long long>(std::min<long long>((long long)c->sms * per_sm, P.ncls[g]), max_grid)
-                         : 0;
-    S = std::max(S, grid[i]);
+  struct Cand {
+    int w, cap, grid;
+  };
+  std::vector<Cand> cand;
+  for (int w : {1, 2, 4}) {
+    const int occ = blk_occ(c, f32, w, P.gb[g], P.gm[g]);
+    if (occ < 1) continue;
+    for (int cap : {occ, cap_rule(n, c->sms, occ)}) {
+      const int grid = (int)std::min<long long>(std::min<long long>((long long)c->sms * cap, n), max_grid);
+      bool dup = grid < 1;
+      for (const Cand& x : cand) dup = dup || (x.w == w && x.grid == grid);
+      if (!dup) cand.push_back({w, cap, grid});
+    }
   }
-  if (S < 1) return NEGF_OK;
+  if (cand.empty()) return NEGF_OK;
   cudaStream_t s = c->stream;
+  const int* order = (const int*)B.order.p + P.ooff[g];
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return set_err(c, NEGF_ECUDA, "event creation failed");
+  int rc = NEGF_OK;
+  for (int w : {1, 2, 4}) {   // load each kernel once
+    bool has = false;
+    for (const Cand& x : cand) has = has || x.w == w;
+    if (!has) continue;
+    const SweepArgs a = group_args(P, g, order, 1, nullptr, nullptr);
+    if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess ||
+        launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], 1, w, s)) {
+      rc = set_err(c, NEGF_ECUDA, "tuning launch failed");
+      break;
+    }
+    ++c->launches;
+  }
   float best = 0.0f;
   int bi = -1;
-  int rc = NEGF_OK;
-  for (int rep = 0; rep < 2 && !rc; ++rep)
-    for (int i = 0; i < 3 && !rc; ++i) {
-      if (grid[i] < 1) continue;
-      const SweepArgs a = group_args(P, g, (const int*)B.order.p + P.ooff[g], S, nullptr, nullptr);
-      if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
-          launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], grid[i], cand[i], s) ||
-          cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
-        rc = set_err(c, NEGF_ECUDA, "width tuning launch failed");
-        break;
-      }
-      ++c->launches;
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep == 1 && (bi < 0 || ms < best)) {
-        best = ms;
-        bi = i;
-      }
+  for (size_t i = 0; i < cand.size() && !rc; ++i) {
+    const SweepArgs a = group_args(P, g, order, n, nullptr, nullptr);
+    if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+        launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], cand[i].grid, cand[i].w, s) ||
+        cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = set_err(c, NEGF_ECUDA, "tuning launch failed");
+      break;
     }
+    ++c->launches;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (bi < 0 || ms < best) {
+      best = ms;
+      bi = (int)i;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
-  c->blk_width[width_key(f32, P.gb[g], P.gm[g])] = cand[bi];
-  P.gw[g] = cand[bi];
-  P.grid[g] = std::max(1, grid[bi]);
+  const Cand& x = cand[bi];
+  c->blk_tuned[std::make_tuple((int)f32, P.gb[g], P.gm[g], n)] = std::make_pair(x.w, x.cap);
+  c->blk_last[std::make_tuple((int)f32, P.gb[g], P.gm[g])] = std::make_pair(x.w, x.cap);
+  P.gw[g] = x.w;
+  P.gcap[g] = x.cap;
+  P.grid[g] = std::max(1, x.grid);
   return NEGF_OK;
 }
 
@@ -321,11 +366,13 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     if (c->opts.blk_warps > 0) {
       P.gw[g] = c->opts.blk_warps;
     } else if (c->opts.blk_warps == 0) {
-      auto it = c->blk_width.find(width_key(group_f32(g), P.gb[g], P.gm[g]));
-      if (it != c->blk_width.end())
-        P.gw[g] = it->second;
-      else
+      auto it = c->blk_tuned.find(std::make_tuple((int)group_f32(g), P.gb[g], P.gm[g], P.ncls[g]));
+      if (it != c->blk_tuned.end()) {
+        P.gw[g] = it->second.first;
+        P.gcap[g] = it->second.second;
+      } else {
         tune_g[g] = P.ncls[g] >= c->sms && capst == cudaStreamCaptureStatusNone;
+      }
     }
   }
 
@@ -350,8 +397,15 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     } else {
       const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16, P.gw[g]);
       if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
-      per_sm = sweep_blk_occupancy_t(f32, P.gw[g], P.gb[g], P.gm[g]);
+      const int occ = blk_occ(c, f32, P.gw[g], P.gb[g], P.gm[g]);
+      per_sm = P.gcap[g] > 0 ? std::min(occ, P.gcap[g]) : cap_rule(P.ncls[g], c->sms, occ);
       wpb = 1;   // one lane (item) per CTA
+      if (tune_g[g]) {   // staging for the widest trial grid
+        int occ_max = occ;
+        for (int w : {1, 2, 4}) occ_max = std::max(occ_max, blk_occ(c, f32, w, P.gb[g], P.gm[g]));
+        const int tgrid = std::max(1, std::min(c->sms * occ_max, P.ncls[g]));
+        stage_bytes = std::max(stage_bytes, P.stride[g] * tgrid);
+      }
     }
     const int need = cls < 2 ? (P.ncls[g] + wpb - 1) / wpb : P.ncls[g];
     P.grid[g] = std::max(1, std::min(c->sms * per_sm, need));
@@ -857,11 +911,12 @@ int negf_kernel_time(negf_ctx* c, double* sweep_ms, uint64_t* sweeps) {
   return NEGF_OK;
 }
 
-int negf_blk_width(negf_ctx* c, int fp32, int b, int m, int* warps) {
+int negf_blk_width(negf_ctx* c, int fp32, int b, int m, int* warps, int* ctas_per_sm) {
   if (!c || !warps) return NEGF_EINVAL;
-  auto it = c->blk_width.find(width_key(fp32 != 0, b, m));
-  if (it == c->blk_width.end()) return NEGF_EINVAL;
-  *warps = it->second;
+  auto it = c->blk_last.find(std::make_tuple(fp32 != 0 ? 1 : 0, b, m));
+  if (it == c->blk_last.end()) return NEGF_EINVAL;
+  *warps = it->second.first;
+  if (ctas_per_sm) *ctas_per_sm = it->second.second;
   return NEGF_OK;
 }
 

@@ -7,6 +7,8 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "../../include/negf.h"
@@ -42,6 +44,7 @@ struct ChainData {
   std::vector<double> Hdiag, Hup;  // interleaved complex
   double g_b = 1.0;
   bool h_set = false;
+  bool h_sym = false;   // every H_ll real symmetric and every H_{l,l+1} real
   HostLead lead[2];
   // device copies
   DBuf dHdiag, dHup, dcs_cnt, dcs_idx, dcs_val, drs_cnt, drs_idx, drs_val, dhsq;
@@ -94,8 +97,10 @@ struct Ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   double prof_ms = 0.0;
   uint64_t prof_count = 0;
-  // CTA widths chosen by the autotuner, keyed by (element type, b, m)
-  std::map<long long, int> blk_width;
+  // launch shapes (CTA width, resident CTAs per SM) chosen by the autotuner of the
+  // wide-block sweep, keyed by (element type, b, m, items); the latest per (type, b, m)
+  std::map<std::tuple<int, int, int, int>, std::pair<int, int>> blk_tuned;
+  std::map<std::tuple<int, int, int>, std::pair<int, int>> blk_last;
   // serving state (serve.cu)
   struct Serve* serve = nullptr;
   std::mutex serve_mu;
@@ -136,6 +141,7 @@ struct Plan {
   int n_items = 0, block_threads = 256;
   int grid[NGROUPS] = {0}, ooff[NGROUPS] = {0}, ncls[NGROUPS] = {0};
   int gb[NGROUPS] = {0}, gm[NGROUPS] = {0}, gw[NGROUPS] = {0};   // bmax, mmax, warps of wide-block groups
+  int gcap[NGROUPS] = {0};                                          // tuned resident CTAs per SM (0: rule)
   long long stride[NGROUPS] = {0};
   long long tpos = 0;
   std::vector<unsigned char> edge_flag;   // per real energy of each device (tbase order, chain 0)

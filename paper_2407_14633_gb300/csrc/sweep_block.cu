@@ -48,9 +48,10 @@ __device__ __forceinline__ cx<T> tc(cd v) {
   return mk((T)v.re, (T)v.im);
 }
 
-// Outputs o0 and o1 = o0 + NT of C = [Add +] A (R x K, lda) * B (K x N, ldb): two partial
-// sums per output (even and odd k) keep eight independent FMA chains in flight.  Every
-// output is evaluated in the same order whichever thread computes it.
+// Outputs o0 and o1 = o0 + NT of C = [Add +] A (R x K, lda) * B (K x N, ldb), one
+// accumulator each in k order (on GB300 a dependent FP64 multiply-add issues as soon as the
+// narrow FP64 pipe is free again, so two chains per thread are enough).  Every output is
+// evaluated in the same order whichever thread computes it.
 template <typename T, int NT>
 __device__ __forceinline__ void dot2(cx<T>& v0, cx<T>& v1, int o0, int tot, const cx<T>* A, int lda,
                                      const cx<T>* B, int ldb, int K, int N, const cx<T>* Add, int ldadd) {
@@ -62,31 +63,86 @@ __device__ __forceinline__ void dot2(cx<T>& v0, cx<T>& v1, int o0, int tot, cons
   const cx<T>* a1 = A + r1 * lda;
   const cx<T>* b0 = B + c0;
   const cx<T>* b1 = B + c1;
-  cx<T> s00 = cz<T>(), s01 = cz<T>(), s10 = cz<T>(), s11 = cz<T>();
-  int k = 0;
-  for (; k + 1 < K; k += 2) {
-    s00 = cmac(s00, a0[k], b0[k * ldb]);
-    s10 = cmac(s10, a1[k], b1[k * ldb]);
-    s01 = cmac(s01, a0[k + 1], b0[(k + 1) * ldb]);
-    s11 = cmac(s11, a1[k + 1], b1[(k + 1) * ldb]);
+  cx<T> s0 = cz<T>(), s1 = cz<T>();
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    s0 = cmac(s0, a0[k], b0[k * ldb]);
+    s1 = cmac(s1, a1[k], b1[k * ldb]);
   }
-  if (k < K) {
-    s00 = cmac(s00, a0[k], b0[k * ldb]);
-    s10 = cmac(s10, a1[k], b1[k * ldb]);
-  }
-  v0 = s00 + s01;
-  v1 = s10 + s11;
+  v0 = s0;
+  v1 = s1;
   if (Add) {
     v0 = v0 + Add[r0 * ldadd + c0];
     v1 = v1 + Add[r1 * ldadd + c1];
   }
 }
 
+// One output o of the same product, same order.
+template <typename T>
+__device__ __forceinline__ cx<T> dot1(int o, const cx<T>* A, int lda, const cx<T>* B, int ldb, int K, int N,
+                                      const cx<T>* Add, int ldadd) {
+  const int r = o / N, c = o - r * N;
+  const cx<T>* a = A + r * lda;
+  const cx<T>* bc = B + c;
+  cx<T> v = cz<T>();
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) v = cmac(v, a[k], bc[k * ldb]);
+  if (Add) v = v + Add[r * ldadd + c];
+  return v;
+}
+
+// One output o computed by a whole warp: lane j takes the terms k = j and j + 32 (K <= 64),
+// then a fixed butterfly sums the lanes; every lane returns the result.
+template <typename T>
+__device__ __forceinline__ cx<T> dot_split(int o, const cx<T>* A, int lda, const cx<T>* B, int ldb, int K, int N,
+                                           const cx<T>* Add, int ldadd, int lane) {
+  const int r = o / N, c = o - r * N;
+  cx<T> p = cz<T>();
+  if (lane < K) p = cmac(p, A[r * lda + lane], B[lane * ldb + c]);
+  if (lane + 32 < K) p = cmac(p, A[r * lda + lane + 32], B[(lane + 32) * ldb + c]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    p.re += __shfl_xor_sync(0xffffffffu, p.re, off);
+    p.im += __shfl_xor_sync(0xffffffffu, p.im, off);
+  }
+  if (Add) p = p + Add[r * ldadd + c];
+  return p;
+}
+
+// Output split of a product with tot = R N outputs.  When tot mod 32 <= SPLIT_LEFT, the first
+// tot - tot mod 32 outputs go one per thread (pairs o, o + NT share a pass, a last unpaired
+// pass takes one output) and the few left over are summed across warp 0 (dot_split), so no
+// pass is half empty: 17 x 17 = 289 = 9 x 32 + 1 costs 9 thread-outputs and one split
+// output instead of 10 thread-outputs.  Otherwise every output goes one per thread in pairs.
+// Which rule an output follows depends on tot only, never on the CTA width.
+constexpr int SPLIT_LEFT = 4;
+__device__ __forceinline__ bool split_mode(int tot) { return (tot & 31) <= SPLIT_LEFT; }
+
 // C (R x N, ldc) = [Add +] A (R x K, lda) * B (K x N, ldb)
 template <typename T, int NT>
 __device__ __forceinline__ void bgemm(cx<T>* C, int ldc, const cx<T>* A, int lda, const cx<T>* B, int ldb,
                                       int R, int K, int N, const cx<T>* Add, int ldadd, int tid) {
   const int tot = R * N;
+  if (split_mode(tot)) {
+    const int main = tot & ~31;   // warp-uniform branches below
+    for (int o0 = tid; o0 < main; o0 += 2 * NT) {
+      const int o1 = o0 + NT;
+      if (o1 < main) {
+        cx<T> v0, v1;
+        dot2<T, NT>(v0, v1, o0, tot, A, lda, B, ldb, K, N, Add, ldadd);
+        C[(o0 / N) * ldc + o0 % N] = v0;
+        C[(o1 / N) * ldc + o1 % N] = v1;
+      } else {
+        C[(o0 / N) * ldc + o0 % N] = dot1(o0, A, lda, B, ldb, K, N, Add, ldadd);
+      }
+    }
+    if (tid < 32)
+      for (int o = main; o < tot; ++o) {
+        const cx<T> v = dot_split(o, A, lda, B, ldb, K, N, Add, ldadd, tid);
+        if (tid == 0) C[(o / N) * ldc + o % N] = v;
+      }
+    return;
+  }
   for (int o0 = tid; o0 < tot; o0 += 2 * NT) {
     cx<T> v0, v1;
     dot2<T, NT>(v0, v1, o0, tot, A, lda, B, ldb, K, N, Add, ldadd);
@@ -96,17 +152,38 @@ __device__ __forceinline__ void bgemm(cx<T>* C, int ldc, const cx<T>* A, int lda
   }
 }
 
-// The same product held in registers (at most 2 * MAXP outputs per thread), so that it can
-// overwrite one of its operands: bgemm_r, a CTA barrier, then store_r.
-constexpr int MAXP = 6;
+// The same product held in registers (at most 2 * MAXP outputs per thread, plus one split
+// output on lanes 0 .. SPLIT_LEFT - 1 of warp 0), so that it can overwrite one of its
+// operands: bgemm_r, a CTA barrier, then store_r.
+constexpr int MAXP = 5;
 template <typename T>
 struct RegTile {
   cx<T> v[2 * MAXP];
+  cx<T> lv;
 };
 template <typename T, int NT>
 __device__ __forceinline__ void bgemm_r(RegTile<T>& t, const cx<T>* A, int lda, const cx<T>* B, int ldb, int R, int K,
                                         int N, const cx<T>* Add, int ldadd, int tid) {
   const int tot = R * N;
+  if (split_mode(tot)) {
+    const int main = tot & ~31;
+#pragma unroll
+    for (int p = 0; p < MAXP; ++p) {
+      const int o0 = tid + p * 2 * NT;
+      if (o0 < main) {
+        if (o0 + NT < main)
+          dot2<T, NT>(t.v[2 * p], t.v[2 * p + 1], o0, tot, A, lda, B, ldb, K, N, Add, ldadd);
+        else
+          t.v[2 * p] = dot1(o0, A, lda, B, ldb, K, N, Add, ldadd);
+      }
+    }
+    if (tid < 32)
+      for (int q = 0; q < tot - main; ++q) {
+        const cx<T> v = dot_split(main + q, A, lda, B, ldb, K, N, Add, ldadd, tid);
+        if (tid == q) t.lv = v;
+      }
+    return;
+  }
 #pragma unroll
   for (int p = 0; p < MAXP; ++p) {
     const int o0 = tid + p * 2 * NT;
@@ -116,11 +193,97 @@ __device__ __forceinline__ void bgemm_r(RegTile<T>& t, const cx<T>* A, int lda, 
 template <typename T, int NT>
 __device__ __forceinline__ void store_r(cx<T>* C, int ldc, const RegTile<T>& t, int R, int N, int tid) {
   const int tot = R * N;
+  const bool split = split_mode(tot);
+  const int main = split ? (tot & ~31) : tot;
 #pragma unroll
   for (int p = 0; p < MAXP; ++p) {
     const int o0 = tid + p * 2 * NT, o1 = o0 + NT;
-    if (o0 < tot) C[(o0 / N) * ldc + o0 % N] = t.v[2 * p];
-    if (o1 < tot) C[(o1 / N) * ldc + o1 % N] = t.v[2 * p + 1];
+    if (o0 < main) C[(o0 / N) * ldc + o0 % N] = t.v[2 * p];
+    if (o1 < main) C[(o1 / N) * ldc + o1 % N] = t.v[2 * p + 1];
+  }
+  if (split && tid < tot - main) C[((main + tid) / N) * ldc + (main + tid) % N] = t.lv;
+}
+
+// Upper triangle of a symmetric b x b result, row by row: index t -> (r, c), r <= c.  Row r
+// starts at r b - r (r - 1) / 2; counting from the end, u = T - 1 - t falls in the block of
+// k = b - 1 - r rows, found from the triangular root of u (exact in FP32 for b <= 64).
+__device__ __forceinline__ void tri_rc(int t, int b, int& r, int& c) {
+  const int u = b * (b + 1) / 2 - 1 - t;
+  int k = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
+  if ((k + 1) * (k + 2) / 2 <= u) ++k;
+  if (k * (k + 1) / 2 > u) --k;
+  r = b - 1 - k;
+  c = b - 1 - (u - k * (k + 1) / 2);
+}
+
+// Upper triangle of Add + W Z^T (all b x b; W Z^T is symmetric when it equals Z G Z^T with G
+// symmetric), one output per thread and pass, into registers.
+template <typename T, int NT>
+__device__ __forceinline__ void bgemm_symt_r(RegTile<T>& t, const cx<T>* W, const cx<T>* Z, const cx<T>* Add, int b,
+                                             int tid) {
+  const int tot = b * (b + 1) / 2;
+#pragma unroll
+  for (int p = 0; p < MAXP + 1; ++p) {   // b (b + 1) / 2 <= (MAXP + 1) NT when b^2 <= 2 MAXP NT
+    const int o = tid + p * NT;
+    if (o < tot) {
+      int r, c;
+      tri_rc(o, b, r, c);
+      const cx<T>* w = W + r * b;
+      const cx<T>* z = Z + c * b;
+      cx<T> v = cz<T>();
+#pragma unroll 4
+      for (int k = 0; k < b; ++k) v = cmac(v, w[k], z[k]);
+      t.v[p] = v + Add[r * b + c];
+    }
+  }
+}
+// A := (A + A^T) / 2 in place, one (r, c) pair per thread.  For a chain with complex
+// symmetric Green's functions the computed inverse gL_l is symmetric only up to rounding
+// times its condition number (large near a surface state of the half chain); averaging keeps
+// it the inverse of a nearby symmetric matrix, which the symmetric G_ll update needs.
+template <typename T, int NT>
+__device__ __forceinline__ void symmetrize(cx<T>* A, int b, int tid) {
+  const int tot = b * (b + 1) / 2;
+  for (int o = tid; o < tot; o += NT) {
+    int r, c;
+    tri_rc(o, b, r, c);
+    if (r == c) continue;
+    const cx<T> v = scale(A[r * b + c] + A[c * b + r], T(0.5));
+    A[r * b + c] = v;
+    A[c * b + r] = v;
+  }
+}
+
+// The same, written straight to C (C must not alias W, Z or Add).
+template <typename T, int NT>
+__device__ __forceinline__ void bgemm_symt(cx<T>* C, const cx<T>* W, const cx<T>* Z, const cx<T>* Add, int b,
+                                           int tid) {
+  const int tot = b * (b + 1) / 2;
+  for (int o = tid; o < tot; o += NT) {
+    int r, c;
+    tri_rc(o, b, r, c);
+    const cx<T>* w = W + r * b;
+    const cx<T>* z = Z + c * b;
+    cx<T> v = cz<T>();
+#pragma unroll 4
+    for (int k = 0; k < b; ++k) v = cmac(v, w[k], z[k]);
+    v = v + Add[r * b + c];
+    C[r * b + c] = v;
+    C[c * b + r] = v;
+  }
+}
+template <typename T, int NT>
+__device__ __forceinline__ void store_sym(cx<T>* C, const RegTile<T>& t, int b, int tid) {
+  const int tot = b * (b + 1) / 2;
+#pragma unroll
+  for (int p = 0; p < MAXP + 1; ++p) {   // b (b + 1) / 2 <= (MAXP + 1) NT when b^2 <= 2 MAXP NT
+    const int o = tid + p * NT;
+    if (o < tot) {
+      int r, c;
+      tri_rc(o, b, r, c);
+      C[r * b + c] = t.v[p];
+      C[c * b + r] = t.v[p];
+    }
   }
 }
 
@@ -230,7 +393,7 @@ __device__ void binv(cx<T>* A, int b, cx<T>* col, int* perm, float* rbest, int* 
         r[u] = A[k * b + j];
       }
 #pragma unroll
-      for (int u = 0; u < 3; ++u) x[u] = cmac(x[u], cz<T>() - f[u], r[u]);
+      for (int u = 0; u < 3; ++u) x[u] = cmsub(x[u], f[u], r[u]);
 #pragma unroll
       for (int u = 0; u < 3; ++u)
         if (q[u] >= 0) A[q[u]] = x[u];
@@ -305,15 +468,16 @@ __device__ __forceinline__ void times_hdn(cx<T>* C, const cx<T>* M, int R, int b
 // elements, then FP64 lead rows (2 m complex + 2 m real), b pivot ints and reductions.
 //   FP32, two-sided backward:              NM = 6, NV = 3
 //   FP64, Dyson backward:                  NM = 4, NV = 3
-//   FP64, Dyson, products in registers:    NM = 3, NV = 2 (compact; when every b x b and
-//                                          b x m product fits 2 MAXP outputs per thread)
+//   FP64, Dyson, products in registers:    NM = 3, NV = 1 (compact; when every b x b and
+//                                          b x m product fits 2 MAXP outputs per thread;
+//                                          R_l of the backward sweep shares the gL_l buffer)
 __host__ __device__ bool sweep_blk_compact(int b, int m, int esize, int warps) {
   const int cap = 2 * MAXP * 32 * warps;
   return esize == 16 && b * b <= cap && b * m <= cap;
 }
 __host__ __device__ size_t sweep_blk_smem_bytes_t(int b, int m, int esize, int warps) {
   const bool cmp = sweep_blk_compact(b, m, esize, warps);
-  const int nm = esize == 8 ? 6 : (cmp ? 3 : 4), nv = cmp ? 2 : 3;
+  const int nm = esize == 8 ? 6 : (cmp ? 3 : 4), nv = cmp ? 1 : 3;
   size_t per = (size_t)(nm * b * b + nv * b * m + b) * esize;
   per = (per + 15) & ~(size_t)15;
   per += (size_t)2 * m * 16 + (size_t)2 * m * 8 + (size_t)(b + 1) * 4 + 8 * 8 + 8 * 4 + 8 * 4;
@@ -351,10 +515,10 @@ __device__ __forceinline__ void alpha_minus(cx<T>* out, const cx<T>* Sub, int l,
 }
 
 template <typename T, int NW, bool TWO, bool CMP>
-__global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bmax, int mmax) {
+__global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) sweep_blk_kernel(SweepArgs a, int bmax, int mmax) {
   constexpr int NT = 32 * NW;
   constexpr int NM = TWO ? 6 : (CMP ? 3 : 4);
-  constexpr int NV = CMP ? 2 : 3;
+  constexpr int NV = CMP ? 1 : 3;
   extern __shared__ __align__(16) unsigned char sm_blk[];
   const int tid = threadIdx.x;
   const int bb = bmax * bmax, bm = bmax * mmax;
@@ -365,7 +529,7 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
   cx<T>* M4 = M3 + bb;   // two-sided only
   cx<T>* M5 = M4 + bb;   // two-sided only
   cx<T>* V0 = M0 + NM * bb;
-  cx<T>* V1 = V0 + bm;
+  cx<T>* V1 = V0 + bm;   // not in the compact layout
   cx<T>* V2 = V1 + bm;   // not in the compact layout
   cx<T>* col = V0 + NV * bm;
   size_t off = (size_t)(NM * bb + NV * bm + bmax) * sizeof(cx<T>);
@@ -485,6 +649,10 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
         alpha_minus<T, NW>(A, nullptr, 0, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);
       }
       binv<T, NW>(A, b, col, perm, redf, redi, tid);
+      if (!TWO && C.sym) {
+        symmetrize<T, NT>(A, b, tid);
+        csync<NW>();
+      }
       // stage gL_l (and R_l)
       cx<T>* sg = reinterpret_cast<cx<T>*>(stage + (long long)l * lstride);
       for (int o = tid; o < nn; o += NT) {
@@ -508,16 +676,22 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
     //  Dyson variant:     G (P: gL_{L-1} = G_{L-1,L-1}), Gl, Z, Wm
     //  two-sided variant: G, Gr = gR_{l+1}, Wk, W1, GlB = gL_l, GpB = gL_{l-1}
     //  both:              K, Kn (drain column factor), Rl (R_l)
-    //  compact Dyson:     G, Gl, Z; K (in place), Rl; Wm and the new G in registers
+    //  compact Dyson:     G, Gl (gL_l, then R_l), Z; K (in place); Wm and the new G in
+    //                     registers
     cx<T>* G = P;
     cx<T>* Gl = A;       // Dyson: gL_l;  two-sided: work matrix Wk
     cx<T>* Z = X;        // Dyson: Z;     two-sided: W1
     cx<T>* Wm = M3;      // Dyson: Wm;    two-sided: Gr
     cx<T>* GlB = M4;     // two-sided only
     cx<T>* GpB = M5;     // two-sided only
-    cx<T>* K = (R == V0) ? V1 : V0;
+    // compact: K takes V0, R_l lives in the Gl buffer (loaded after each G_ll update)
+    cx<T>* K = CMP ? V0 : ((R == V0) ? V1 : V0);
     cx<T>* Kn = CMP ? K : V2;
-    cx<T>* Rl = R;
+    cx<T>* Rl = CMP ? Gl : R;
+    if (CMP && real) {
+      for (int o = tid; o < b * mS; o += NT) Rl[o] = R[o];   // R_{L-1} out of V0
+      csync<NW>();
+    }
     if (real) {
       // K_{L-1} = G_{L-1,L-1} L_D: K[r][j] = sum_s G[r][site_s] w^{j s} sqrt(gamma_j/m)
       for (int o = tid; o < b * mD; o += NT) {
@@ -548,7 +722,7 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
         const cd* cval = C.cs_val + (long long)l * b * kmax;
         if (!TWO) {
           for (int o = tid; o < nn; o += NT) Gl[o] = sg[o];
-          if (real)
+          if (real && !CMP)
             for (int o = tid; o < b * mS; o += NT) Rl[o] = sg[bb + o];
           csync<NW>();
           times_hup<T, NT>(Z, Gl, b, b, ccnt, cidx, cval, kmax, tid);                // Z = gL_l H_{l,l+1}
@@ -563,19 +737,32 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
               store_r<T, NT>(K, mD, rt, b, mD, tid);
             }
             csync<NW>();
-            hdn_times<T, NT>(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, tid);           // Z = H_{l+1,l} gL_l
-            csync<NW>();
-            bgemm_r<T, NT>(rt, G, b, Z, b, b, b, b, Gl, b, tid);                      // gL_l + Wm Z
-            csync<NW>();
-            store_r<T, NT>(G, b, rt, b, b, tid);
+            if (C.sym) {
+              // G_ll = gL_l + Z G_{l+1} Z^T is symmetric: upper triangle, mirrored
+              bgemm_symt_r<T, NT>(rt, G, Z, Gl, b, tid);
+              csync<NW>();
+              store_sym<T, NT>(G, rt, b, tid);
+            } else {
+              hdn_times<T, NT>(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, tid);         // Z = H_{l+1,l} gL_l
+              csync<NW>();
+              bgemm_r<T, NT>(rt, G, b, Z, b, b, b, b, Gl, b, tid);                    // gL_l + Wm Z
+              csync<NW>();
+              store_r<T, NT>(G, b, rt, b, b, tid);
+            }
+            if (real)
+              for (int o = tid; o < b * mS; o += NT) Rl[o] = sg[bb + o];             // R_l into Gl
             csync<NW>();
           } else {
             if (real) bgemm<T, NT>(Kn, mD, Z, b, K, mD, b, b, mD, nullptr, 0, tid);  // K_l = Z K_{l+1}
             bgemm<T, NT>(Wm, b, Z, b, G, b, b, b, b, nullptr, 0, tid);               // Wm = Z G_{l+1}
             csync<NW>();
-            hdn_times<T, NT>(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, tid);           // Z = H_{l+1,l} gL_l
-            csync<NW>();
-            bgemm<T, NT>(G, b, Wm, b, Z, b, b, b, b, Gl, b, tid);                     // G = gL_l + Wm Z
+            if (C.sym) {
+              bgemm_symt<T, NT>(G, Wm, Z, Gl, b, tid);                                // gL_l + Wm Z^T
+            } else {
+              hdn_times<T, NT>(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, tid);         // Z = H_{l+1,l} gL_l
+              csync<NW>();
+              bgemm<T, NT>(G, b, Wm, b, Z, b, b, b, b, Gl, b, tid);                   // G = gL_l + Wm Z
+            }
             csync<NW>();
           }
         } else {
@@ -635,8 +822,8 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk_kernel(SweepArgs a, int bma
         if (tid < 32)
           for (int r = tid; r < b; r += 32) {
             T as = T(0), ad = T(0);
-            for (int j = 0; j < mS; ++j) as += abs2(Pm[r * mS + j]);
-            for (int j = 0; j < mD; ++j) ad += abs2(K[r * mD + j]);
+            for (int j = 0; j < mS; ++j) as = fma(Pm[r * mS + j].im, Pm[r * mS + j].im, fma(Pm[r * mS + j].re, Pm[r * mS + j].re, as));
+            for (int j = 0; j < mD; ++j) ad = fma(K[r * mD + j].im, K[r * mD + j].im, fma(K[r * mD + j].re, K[r * mD + j].re, ad));
             vr[r / spr] += wS * (double)as + wD * (double)ad;
             if (a.resid) {
               const double gim = (double)G[r * b + r].im;

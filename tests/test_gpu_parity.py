@@ -72,6 +72,34 @@ def test_realspace_blocks(ctx, n_tube, N):
     check(p, r, run_oracle(p, chunk=16))
 
 
+@pytest.mark.parametrize("n_tube,N,blk_warps", [(7, 16, 1), (17, 9, 1), (17, 9, 4), (26, 5, 2)])
+def test_flux_threaded_tube_general_blocks(n_tube, N, blk_warps):
+    """A flux through the tube (H_ll += i d (S - S^T), a Peierls phase on the ring bonds)
+    makes every block complex and the Green's functions non-symmetric: the general update
+    path, for the compact and the wider shared-memory layouts."""
+    from paper_2407_14633_gb300 import negf
+    U = synth.sinusoid_profile(N, 6)
+    p = case_params("real", N, 41, 9, U, mu_D=-0.3, n_tube=n_tube, U_S=0.0, U_D=-0.3)
+    dev_o = omdl.cnt_build("real", n_tube, p["t"], N, p["U_S"], p["U_D"])
+    ch = dev_o.chains[0]
+    S = omdl.shift_matrix(n_tube)
+    ch.Hdiag = ch.Hdiag + 1j * 0.15 * (S - S.T)[None, :, :]
+    ch.Hup = ch.Hup * np.exp(1j * 0.3)
+    o = ochg.negf_evaluate(dev_o, U, ogr_grid(p), chunk=16)
+    with negf.Context(blk_warps=blk_warps) as c2:
+        dev = lib_device(c2, "real", n_tube, p["t"], N, p["U_S"], p["U_D"])
+        c2.set_hamiltonian(dev, 0, ch.Hdiag.reshape(-1), ch.Hup.reshape(-1), 1.0)
+        c2.set_potential(dev, U)
+        lib_grid(c2, dev, p)
+        r = c2.compute([dev])[0]
+    check(p, r, o)
+
+
+def ogr_grid(p):
+    from tests.cases import oracle_grid
+    return oracle_grid(p)
+
+
 def test_zero_bias_current_is_zero(ctx):
     N = 30
     U = 0.05 * np.sin(np.arange(N))
