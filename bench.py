@@ -50,19 +50,28 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def algorithmic_flops(b, m, nnz, L, n_real, n_cont, sym=True):
-    """FLOPs of one NEGF evaluation as the block sweep computes it (8 per complex MAC).
-    Per layer, real-axis lane: block inverse b^3, lead-column products R, K, G R (3 b^2 m),
-    the G_ll update Z G_{l+1} (b^3) then (Z G_{l+1}) Z^T + gL_l, and the sparse coupling
-    products.  For a chain with complex symmetric Green's functions (sym: real H blocks and
-    real lead rows, as for the nanotube) the second product is the upper triangle only,
-    b^2 (b + 1) / 2, and three coupling products (3 b^2 nnz) remain; otherwise b^3 and four.
-    Contour lane: the same without the lead-column products."""
+def lane_flops(b, m, nnz, L, real, sym):
+    """FLOPs of one lane (one energy, all L layers) of the block sweep as it computes it
+    (8 per complex MAC).  Per layer: block inverse b^3; the G_ll update Z G_{l+1} (b^3) then
+    (Z G_{l+1})(H_{l+1,l} gL_l) + gL_l, b^3, or for a lane on the complex-symmetric form only
+    the upper triangle, b^2 (b + 1) / 2; the sparse coupling products, 4 b^2 nnz (3 on the
+    symmetric form, which does not form H_{l+1,l} gL_l); real-axis lanes add the lead-column
+    products R, K and G R, 3 b^2 m."""
     upd = b ** 3 + (b * b * (b + 1) // 2 if sym else b ** 3)
     sparse = (3 if sym else 4) * b * b * nnz
-    real = b ** 3 + upd + 3 * b * b * m + sparse
-    cont = b ** 3 + upd + sparse
-    return 8.0 * L * (n_real * real + n_cont * cont)
+    return 8.0 * L * (b ** 3 + upd + sparse + (3 * b * b * m if real else 0))
+
+
+def algorithmic_flops(b, m, nnz, L, n_real, n_cont, sym=True):
+    """FLOPs of one NEGF evaluation with every lane on the given update form."""
+    return n_real * lane_flops(b, m, nnz, L, True, sym) + n_cont * lane_flops(b, m, nnz, L, False, sym)
+
+
+def counted_flops(b, m, nnz, L, lanes):
+    """FLOPs of the lanes counted by negf_sweep_lanes (symmetric / general, real / contour)."""
+    rs, rg, cs, cg = lanes
+    return (rs * lane_flops(b, m, nnz, L, True, True) + rg * lane_flops(b, m, nnz, L, True, False) +
+            cs * lane_flops(b, m, nnz, L, False, True) + cg * lane_flops(b, m, nnz, L, False, False))
 
 
 class Clocks:
@@ -248,14 +257,16 @@ def run_ours(args):
     I_t = torch.empty(1, dtype=torch.float64, device="cuda")
     outs = [dict(n=n_t.data_ptr(), T=T_t.data_ptr(), I=I_t.data_ptr())]
     ctx.kernel_time()
+    ctx.sweep_lanes()
     reps = 3
     for _ in range(reps):
         ctx.compute_device([dev], outs)
     torch.cuda.synchronize()
     sweep_ms, sweeps = ctx.kernel_time()
+    lanes = ctx.sweep_lanes()
     ctx.profile(False)
     sweep_ms /= max(sweeps, 1)
-    flops = algorithmic_flops(17, 17, 1.5, N, n_real, n_cont)
+    flops = counted_flops(17, 17, 1.5, N, lanes) / max(sweeps, 1)
     achieved = flops / (sweep_ms * 1e-3) / 1e12
     props = torch.cuda.get_device_properties(local)
     sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -305,7 +316,11 @@ def run_ours(args):
                      "peak": peak_derived, "unit": "TFLOP/s", "frac": achieved / peak_derived,
                      "peak_kind": "FP64 derived: 2 FMA/clk/SM x SMs x max SM clock",
                      "peak_probe": peak_probe, "frac_of_probe": achieved / peak_probe,
-                     "traffic": traffic, "kernel_ms": sweep_ms, "flops_per_launch": flops},
+                     "traffic": traffic, "kernel_ms": sweep_ms, "flops_per_launch": flops,
+                     "lanes_per_launch": {"real_symmetric": lanes[0] // max(sweeps, 1),
+                                          "real_general": lanes[1] // max(sweeps, 1),
+                                          "contour_symmetric": lanes[2] // max(sweeps, 1),
+                                          "contour_general": lanes[3] // max(sweeps, 1)}},
         "clocks": clocks,
         "self_consistent_solve": sc,
     }
@@ -328,27 +343,51 @@ def run_ours(args):
 
 
 def run_profile_small(args):
-    """Reduced case of the same kernel for ncu captures: (17,0) real space, N = 64 rings and
-    the full grid (2048 real-axis + 128 contour energies, so the same lanes and waves as the
-    bench workload at 1/8 of its length), three NEGF evaluations (no SC loop, no CPU leg)."""
+    """Reduced cases for ncu captures (three NEGF evaluations, no SC loop, no CPU leg).
+
+    rs17 (default): (17,0) real space, N = 64 rings and the full grid (2048 real-axis + 128
+    contour energies, so the same lanes and waves as the bench workload at 1/8 of its length),
+    complex128.  rs17_c64: the same with the complex64 sweep.  mode: eight (17,0) mode-space
+    devices, modes 6 and 5, N = 1000, 4032 + 64 energies each (the thread-per-lane 1 x 1 sweep
+    of the batched and serving workloads), complex128."""
     import torch
     from paper_2407_14633_gb300 import negf, synth
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    prec = negf.PREC_FP32 if args.profile_case == "rs17_c64" else negf.PREC_FP64
     ctx = negf.Context(device=0, stream=stream.cuda_stream, blk_warps=args.blk_warps,
-                       blk_ctas_per_sm=args.blk_ctas)
-    w = synth.realspace_17(N=64)
-    dev = ctx.device_create(w["N"], block=17, rings_per_block=1, n_chains=1)
-    ctx.build_cnt_realspace(dev, 17, w["t"], w["U_S"], w["U_D"])
-    ctx.set_potential(dev, w["U"])
-    ctx.set_grid_spec(dev, w["mu_S"], w["mu_D"], w["kT"], w["eta"], w["E_B"], w["n_real"], w["n_cont"])
+                       blk_ctas_per_sm=args.blk_ctas, precision=prec)
+    n_dev = 1
+    if args.profile_case == "mode":
+        N, n_real, n_cont, n_dev = 1000, 4032, 64, 8
+        w = synth.realspace_17(N=N, n_real=n_real, n_cont=n_cont)
+        devs = [ctx.device_create(N, block=1, rings_per_block=1, n_chains=2) for _ in range(n_dev)]
+        for dev in devs:
+            ctx.build_cnt_modespace(dev, 17, w["t"], [6, 5], w["U_S"], w["U_D"])
+        flops = None
+    else:
+        w = synth.realspace_17(N=64)
+        devs = [ctx.device_create(w["N"], block=17, rings_per_block=1, n_chains=1)]
+        ctx.build_cnt_realspace(devs[0], 17, w["t"], w["U_S"], w["U_D"])
+        flops = algorithmic_flops(17, 17, 1.5, w["N"], w["n_real"], w["n_cont"])
+    for dev in devs:
+        ctx.set_potential(dev, w["U"])
+        ctx.set_grid_spec(dev, w["mu_S"], w["mu_D"], w["kT"], w["eta"], w["E_B"], w["n_real"], w["n_cont"])
     ctx.profile(True)
     for _ in range(3):
-        r = ctx.compute([dev])[0]
+        r = ctx.compute(devs)[0]
     ms, k = ctx.kernel_time()
-    flops = algorithmic_flops(17, 17, 1.5, w["N"], w["n_real"], w["n_cont"])
-    print(json.dumps({"case": "profile_small", "sweep_ms": ms / k, "tflops": flops / (ms / k * 1e-3) / 1e12,
-                      "I": r["I"], "cta_warps": args.blk_warps, "ctas_per_sm": args.blk_ctas}))
+    lanes = ctx.sweep_lanes()
+    if flops:
+        flops = counted_flops(17, 17, 1.5, w["N"], lanes) / max(k, 1)
+    line = {"case": "profile_small", "profile_case": args.profile_case, "sweep_ms": ms / k, "I": r["I"],
+            "cta_warps": args.blk_warps, "ctas_per_sm": args.blk_ctas, "lanes": lanes}
+    if flops:
+        line["tflops"] = flops / (ms / k * 1e-3) / 1e12
+    else:
+        updates = n_dev * w["N"] * 2 * (w["n_real"] + w["n_cont"])
+        line["ring_energy_mode_updates_per_s"] = updates / (ms / k * 1e-3)
+    print(json.dumps(line))
     ctx.close()
     return 0
 
@@ -368,6 +407,8 @@ def main():
                     help="reduced case of the block sweep for ncu captures")
     ap.add_argument("--blk-warps", type=int, default=1,
                     help="CTA width of the block sweep in --profile-small (no tuning launches)")
+    ap.add_argument("--profile-case", default="rs17", choices=["rs17", "rs17_c64", "mode"],
+                    help="which reduced case --profile-small runs")
     ap.add_argument("--blk-ctas", type=int, default=0,
                     help="cap on resident CTAs per SM of the block sweep in --profile-small (0: no cap)")
     args = ap.parse_args()

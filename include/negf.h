@@ -78,7 +78,9 @@ typedef struct negf_ctx negf_ctx;
  * block size, lead width and item count that has at least one item per SM, then cached;
  * smaller batches use the size policy), -1 = the size policy (1 warp up to b = 20, 2 up to
  * 28, else 4), 1 / 2 / 4 = that width.  Results are bitwise the same for every width.  blk_ctas_per_sm: cap on the resident CTAs per SM of
- * that sweep (0 = as many as fit); the grid is the cap times the SMs. */
+ * that sweep (0 = as many as fit); the grid is the cap times the SMs.  general_update: 1 =
+ * never use the complex-symmetric form of the G_ll update, even for chains whose blocks and
+ * lead rows are real (0 = use it there). */
 typedef struct {
   int device_ordinal;
   void* stream;
@@ -90,6 +92,7 @@ typedef struct {
   double growth_threshold;
   int blk_warps;
   int blk_ctas_per_sm;
+  int general_update;
 } negf_opts;
 
 /* Create / destroy a context on one GPU.  opts may be NULL (defaults: device 0, own
@@ -378,6 +381,12 @@ int negf_launch_count(const negf_ctx* ctx, uint64_t* launches);
  * returns (and resets) the summed sweep time in ms and the number of timed sweeps. */
 int negf_profile(negf_ctx* ctx, int enable);
 int negf_kernel_time(negf_ctx* ctx, double* sweep_ms, uint64_t* sweeps);
+/* With profiling on, the sweep of ring blocks wider than 2 also counts its lanes by update
+ * form: lanes[0] real-axis lanes with the complex-symmetric G_ll update, lanes[1] real-axis
+ * lanes with the general one, lanes[2] / lanes[3] the same for contour lanes.  Returns the
+ * counts accumulated since the last call (or since profiling was switched on) and resets
+ * them. */
+int negf_sweep_lanes(negf_ctx* ctx, uint64_t lanes[4]);
 
 /* The launch shape the autotuner last chose for ring blocks of width b with leads of m
  * sites in FP64 (fp32 = 0) or FP32 (fp32 = 1): CTA width in warps and resident CTAs per SM

@@ -86,7 +86,7 @@ Dev* get_dev(Ctx* c, int dev) {
 void free_dev(Ctx* c, Dev* d) {
   for (auto& ch : d->ch) {
     for (DBuf* b : {&ch.dHdiag, &ch.dHup, &ch.dcs_cnt, &ch.dcs_idx, &ch.dcs_val, &ch.drs_cnt, &ch.drs_idx,
-                    &ch.drs_val, &ch.dhsq})
+                    &ch.drs_val, &ch.dhsq, &ch.dHdiag_f, &ch.dcs_val_f, &ch.drs_val_f})
       c->arena.release(*b);
     for (int s = 0; s < 2; ++s)
       for (DBuf* b : {&ch.da1[s], &ch.da2[s], &ch.dat[s], &ch.dsites[s], &ch.dtw[s]})
@@ -134,6 +134,13 @@ int upload_lead(Ctx* c, ChainData& ch, int side) {
 }
 
 // device copies of a chain's Hamiltonian: dense blocks, column-sparse couplings, |h|^2
+// complex64 copy of an interleaved complex128 array
+static int upload_f32(Ctx* c, DBuf& b, const std::vector<double>& v) {
+  std::vector<float> f(std::max<size_t>(v.size(), 2));
+  for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
+  return upload(c, b, f.data(), f.size() * 4);
+}
+
 int upload_chain(Ctx* c, Dev* d, ChainData& ch) {
   const int b = d->block, L = d->L;
   int rc;
@@ -151,6 +158,7 @@ int upload_chain(Ctx* c, Dev* d, ChainData& ch) {
   for (size_t i = 1; i < ch.Hup.size() && ch.h_sym; i += 2)
     if (ch.Hup[i] != 0.0) ch.h_sym = false;
   if ((rc = upload(c, ch.dHdiag, ch.Hdiag.data(), ch.Hdiag.size() * 8))) return rc;
+  if ((rc = upload_f32(c, ch.dHdiag_f, ch.Hdiag))) return rc;
   if ((rc = upload(c, ch.dHup, ch.Hup.data(), std::max<size_t>(ch.Hup.size(), 2) * 8))) return rc;
   int kmax = 1;
   for (int l = 0; l < L - 1; ++l)
@@ -184,6 +192,7 @@ int upload_chain(Ctx* c, Dev* d, ChainData& ch) {
   if ((rc = upload(c, ch.dcs_cnt, cnt.data(), cnt.size() * 4))) return rc;
   if ((rc = upload(c, ch.dcs_idx, idx.data(), idx.size() * 4))) return rc;
   if ((rc = upload(c, ch.dcs_val, val.data(), val.size() * 8))) return rc;
+  if ((rc = upload_f32(c, ch.dcs_val_f, val))) return rc;
   // row-sparse form (row r: entries (column, value)), padded to the same kmax
   int rkmax = 1;
   for (int l = 0; l < L - 1; ++l)
@@ -208,6 +217,7 @@ int upload_chain(Ctx* c, Dev* d, ChainData& ch) {
       }
     if ((rc = upload(c, ch.dcs_idx, idx2.data(), idx2.size() * 4))) return rc;
     if ((rc = upload(c, ch.dcs_val, val2.data(), val2.size() * 8))) return rc;
+    if ((rc = upload_f32(c, ch.dcs_val_f, val2))) return rc;
     ch.kmax = km;
   }
   std::vector<int> rcnt((size_t)nl * b, 0), ridx((size_t)nl * b * km, 0);
@@ -230,6 +240,7 @@ int upload_chain(Ctx* c, Dev* d, ChainData& ch) {
   if ((rc = upload(c, ch.drs_cnt, rcnt.data(), rcnt.size() * 4))) return rc;
   if ((rc = upload(c, ch.drs_idx, ridx.data(), ridx.size() * 4))) return rc;
   if ((rc = upload(c, ch.drs_val, rval.data(), rval.size() * 8))) return rc;
+  if ((rc = upload_f32(c, ch.drs_val_f, rval))) return rc;
   std::vector<double> hsq(nl, 0.0);
   if (b == 1)
     for (int l = 0; l < L - 1; ++l) hsq[l] = ch.Hup[2 * l] * ch.Hup[2 * l] + ch.Hup[2 * l + 1] * ch.Hup[2 * l + 1];

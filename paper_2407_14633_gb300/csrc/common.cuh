@@ -106,6 +106,9 @@ struct ChainView {
   const int* cs_idx;
   const cd* cs_val;
   int kmax;
+  const cf* Hdiag_f;  // complex64 copies of Hdiag, cs_val, rs_val (complex64 sweeps)
+  const cf* cs_val_f;
+  const cf* rs_val_f;
   const double* hsq; // block 1: |H_{l,l+1}|^2 per layer (L-1)
   double g_b;
   int sym;           // real H blocks and real lead rows: every G_ll is complex symmetric
@@ -155,6 +158,7 @@ struct SweepArgs {
   unsigned char* stage;   // staging of the forward sweep, per resident warp
   long long stage_stride; // bytes per resident warp
   int* status;            // device error flag (0 ok)
+  unsigned long long* lane_stats;  // per-form lane counts (profiling; may be null)
 };
 
 // ---------------------------------------------------------------- launchers

@@ -30,7 +30,6 @@ struct Tune {
 
 
 DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
-  (void)c;
   DeviceView v;
   memset(&v, 0, sizeof(v));
   v.n_rings = d->n_rings;
@@ -73,6 +72,9 @@ DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
     cv.rs_idx = (const int*)ch.drs_idx.p;
     cv.rs_val = (const cd*)ch.drs_val.p;
     cv.kmax = ch.kmax;
+    cv.Hdiag_f = (const cf*)ch.dHdiag_f.p;
+    cv.cs_val_f = (const cf*)ch.dcs_val_f.p;
+    cv.rs_val_f = (const cf*)ch.drs_val_f.p;
     cv.hsq = (const double*)ch.dhsq.p;
     cv.g_b = ch.g_b;
     // complex symmetric Green's functions: real symmetric H blocks, real couplings and leads
@@ -81,7 +83,7 @@ DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
     for (int s2 = 0; s2 < 2; ++s2)
       for (const std::vector<double>* f : {&ch.lead[s2].T1, &ch.lead[s2].T2, &ch.lead[s2].tau})
         for (size_t i = 1; i < f->size(); i += 2) lead_real = lead_real && (*f)[i] == 0.0;
-    cv.sym = (ch.h_sym && lead_real) ? 1 : 0;
+    cv.sym = (ch.h_sym && lead_real && !c->opts.general_update) ? 1 : 0;
     for (int s = 0; s < 2; ++s) {
       LeadView& lv = cv.lead[s];
       lv.m = ch.lead[s].m;
@@ -144,6 +146,7 @@ static SweepArgs group_args(const Plan& P, int g, const int* order, int n, doubl
   a.stage = (unsigned char*)B.stage.p;
   a.stage_stride = P.stride[g % 5];
   a.status = (int*)B.status.p;
+  a.lane_stats = nullptr;
   return a;
 }
 
@@ -523,7 +526,8 @@ static int launch_group(Ctx* c, const Plan& P, int g, const int* order, int n, i
                         double* growth) {
   const int cls = group_class(g);
   const bool f32 = group_f32(g);
-  const SweepArgs a = group_args(P, g, order, n, resid, growth);
+  SweepArgs a = group_args(P, g, order, n, resid, growth);
+  if (c->profile && c->lane_stats.p) a.lane_stats = (unsigned long long*)c->lane_stats.p;
   cudaStream_t s = c->stream;
   int rc;
   if (cls == 0)
@@ -888,6 +892,26 @@ extern "C" {
 int negf_profile(negf_ctx* c, int enable) {
   if (!c) return NEGF_EINVAL;
   c->profile = enable != 0;
+  if (c->profile) {
+    cudaSetDevice(c->ordinal);
+    if (!ensure(c, c->lane_stats, 4 * sizeof(unsigned long long))) return NEGF_ENOMEM;
+    if (cudaMemsetAsync(c->lane_stats.p, 0, 4 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+      return set_err(c, NEGF_ECUDA, "counter reset failed");
+  }
+  return NEGF_OK;
+}
+
+int negf_sweep_lanes(negf_ctx* c, uint64_t lanes[4]) {
+  if (!c || !lanes) return NEGF_EINVAL;
+  for (int i = 0; i < 4; ++i) lanes[i] = 0;
+  if (!c->lane_stats.p) return NEGF_OK;
+  cudaSetDevice(c->ordinal);
+  unsigned long long h[4];
+  if (cudaMemcpyAsync(h, c->lane_stats.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->lane_stats.p, 0, sizeof(h), c->stream) != cudaSuccess)
+    return set_err(c, NEGF_ECUDA, "counter read failed");
+  for (int i = 0; i < 4; ++i) lanes[i] = h[i];
   return NEGF_OK;
 }
 

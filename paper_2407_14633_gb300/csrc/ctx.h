@@ -48,6 +48,7 @@ struct ChainData {
   HostLead lead[2];
   // device copies
   DBuf dHdiag, dHup, dcs_cnt, dcs_idx, dcs_val, drs_cnt, drs_idx, drs_val, dhsq;
+  DBuf dHdiag_f, dcs_val_f, drs_val_f;   // complex64 copies for the complex64 sweeps
   DBuf da1[2], da2[2], dat[2], dsites[2], dtw[2];
   int kmax = 0;
 };
@@ -97,6 +98,7 @@ struct Ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
   double prof_ms = 0.0;
   uint64_t prof_count = 0;
+  DBuf lane_stats;   // 4 counters of negf_sweep_lanes
   // launch shapes (CTA width, resident CTAs per SM) chosen by the autotuner of the
   // wide-block sweep, keyed by (element type, b, m, items); the latest per (type, b, m)
   std::map<std::tuple<int, int, int, int>, std::pair<int, int>> blk_tuned;

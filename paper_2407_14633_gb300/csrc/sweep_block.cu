@@ -237,10 +237,17 @@ __device__ __forceinline__ void bgemm_symt_r(RegTile<T>& t, const cx<T>* W, cons
     }
   }
 }
+// Gate of the symmetric G_ll update: largest |gL_l diagonal entry| (1/eV) of a lane.  Away from
+// bound states of the half chain it stays near 1 / |t|, a few 1/eV at band edges; near one it
+// grows like 1 / distance, and the update's rounding error grows like u |gL|^2 / |G|, so at
+// 100 it stays near 1e-12 relative.  (The zigzag end of every half chain of a nanotube carries
+// edge states at the local potential, so lanes crossing one somewhere are common.)
+constexpr double SYM_GL_MAX = 100.0;
+
 // A := (A + A^T) / 2 in place, one (r, c) pair per thread.  For a chain with complex
 // symmetric Green's functions the computed inverse gL_l is symmetric only up to rounding
-// times its condition number (large near a surface state of the half chain); averaging keeps
-// it the inverse of a nearby symmetric matrix, which the symmetric G_ll update needs.
+// times its condition number; averaging keeps it the inverse of a nearby symmetric matrix,
+// which the symmetric G_ll update needs.
 template <typename T, int NT>
 __device__ __forceinline__ void symmetrize(cx<T>* A, int b, int tid) {
   const int tot = b * (b + 1) / 2;
@@ -287,16 +294,37 @@ __device__ __forceinline__ void store_sym(cx<T>* C, const RegTile<T>& t, int b, 
   }
 }
 
+// Hamiltonian data in the sweep's element type (complex64 copies for the complex64 sweep, so
+// that no conversion from FP64 sits in its inner loops)
+template <typename T>
+__device__ __forceinline__ const cx<T>* hdiag_t(const ChainView& C);
+template <>
+__device__ __forceinline__ const cd* hdiag_t<double>(const ChainView& C) { return C.Hdiag; }
+template <>
+__device__ __forceinline__ const cf* hdiag_t<float>(const ChainView& C) { return C.Hdiag_f; }
+template <typename T>
+__device__ __forceinline__ const cx<T>* csval_t(const ChainView& C);
+template <>
+__device__ __forceinline__ const cd* csval_t<double>(const ChainView& C) { return C.cs_val; }
+template <>
+__device__ __forceinline__ const cf* csval_t<float>(const ChainView& C) { return C.cs_val_f; }
+template <typename T>
+__device__ __forceinline__ const cx<T>* rsval_t(const ChainView& C);
+template <>
+__device__ __forceinline__ const cd* rsval_t<double>(const ChainView& C) { return C.rs_val; }
+template <>
+__device__ __forceinline__ const cf* rsval_t<float>(const ChainView& C) { return C.rs_val_f; }
+
 // C (b x N) = H_{l+1,l} M where H_{l+1,l} = Hup_l^dagger: row r uses column r of Hup_l
 template <typename T, int NT>
 __device__ __forceinline__ void hdn_times(cx<T>* C, const cx<T>* M, int ldm, int N, int b, const int* cnt,
-                                          const int* idx, const cd* val, int kmax, int tid) {
+                                          const int* idx, const cx<T>* val, int kmax, int tid) {
   const int tot = b * N;
   for (int o = tid; o < tot; o += NT) {
     const int r = o / N, c = o - r * N;
     cx<T> acc = cz<T>();
     const int n = cnt[r];
-    for (int e = 0; e < n; ++e) acc = cmac_cj(acc, tc<T>(val[r * kmax + e]), M[idx[r * kmax + e] * ldm + c]);
+    for (int e = 0; e < n; ++e) acc = cmac_cj(acc, val[r * kmax + e], M[idx[r * kmax + e] * ldm + c]);
     C[r * N + c] = acc;
   }
 }
@@ -304,13 +332,13 @@ __device__ __forceinline__ void hdn_times(cx<T>* C, const cx<T>* M, int ldm, int
 // C (R x b) = M (R x b) Hup_l: column c uses column c of Hup_l
 template <typename T, int NT>
 __device__ __forceinline__ void times_hup(cx<T>* C, const cx<T>* M, int R, int b, const int* cnt, const int* idx,
-                                          const cd* val, int kmax, int tid) {
+                                          const cx<T>* val, int kmax, int tid) {
   const int tot = R * b;
   for (int o = tid; o < tot; o += NT) {
     const int r = o / b, c = o - r * b;
     cx<T> acc = cz<T>();
     const int n = cnt[c];
-    for (int e = 0; e < n; ++e) acc = cmac(acc, M[r * b + idx[c * kmax + e]], tc<T>(val[c * kmax + e]));
+    for (int e = 0; e < n; ++e) acc = cmac(acc, M[r * b + idx[c * kmax + e]], val[c * kmax + e]);
     C[r * b + c] = acc;
   }
 }
@@ -440,26 +468,26 @@ __device__ __forceinline__ double cta_max(double v, double* red, int tid) {
 // C (b x N) = H_{l,l+1} M: row r uses row r of Hup_l
 template <typename T, int NT>
 __device__ __forceinline__ void hup_times(cx<T>* C, const cx<T>* M, int ldm, int N, int b, const int* cnt,
-                                          const int* idx, const cd* val, int kmax, int tid) {
+                                          const int* idx, const cx<T>* val, int kmax, int tid) {
   const int tot = b * N;
   for (int o = tid; o < tot; o += NT) {
     const int r = o / N, c = o - r * N;
     cx<T> acc = cz<T>();
     const int n = cnt[r];
-    for (int e = 0; e < n; ++e) acc = cmac(acc, tc<T>(val[r * kmax + e]), M[idx[r * kmax + e] * ldm + c]);
+    for (int e = 0; e < n; ++e) acc = cmac(acc, val[r * kmax + e], M[idx[r * kmax + e] * ldm + c]);
     C[r * N + c] = acc;
   }
 }
 // C (R x b) = M H_{l+1,l} = M Hup_l^dagger: column c uses row c of Hup_l, conjugated
 template <typename T, int NT>
 __device__ __forceinline__ void times_hdn(cx<T>* C, const cx<T>* M, int R, int b, const int* cnt, const int* idx,
-                                          const cd* val, int kmax, int tid) {
+                                          const cx<T>* val, int kmax, int tid) {
   const int tot = R * b;
   for (int o = tid; o < tot; o += NT) {
     const int r = o / b, c = o - r * b;
     cx<T> acc = cz<T>();
     const int n = cnt[c];
-    for (int e = 0; e < n; ++e) acc = cmac_cj(acc, tc<T>(val[c * kmax + e]), M[r * b + idx[c * kmax + e]]);
+    for (int e = 0; e < n; ++e) acc = cmac_cj(acc, val[c * kmax + e], M[r * b + idx[c * kmax + e]]);
     C[r * b + c] = acc;
   }
 }
@@ -491,14 +519,13 @@ __device__ __forceinline__ void alpha_minus(cx<T>* out, const cx<T>* Sub, int l,
                                             cd eps, const DeviceView& D, const ChainView& C, const cd* sigS,
                                             const cd* sigD, int tid) {
   constexpr int NT = 32 * NW;
-  const cd* hd = C.Hdiag + (long long)l * b * b;
+  const cx<T>* hd = hdiag_t<T>(C) + (long long)l * b * b;
   const int nn = b * b;
-  for (int o = tid; o < nn; o += NT) {
-    const int r = o / b, c = o - r * b;
-    cd v = mk(-hd[o].re, -hd[o].im);
-    if (r == c) v = v + mk(eps.re - D.U[l * rpb + r / spr], eps.im);
-    out[o] = Sub ? tc<T>(v) - Sub[o] : tc<T>(v);
-  }
+  for (int o = tid; o < nn; o += NT) out[o] = Sub ? mk(-hd[o].re - Sub[o].re, -hd[o].im - Sub[o].im) : mk(-hd[o].re, -hd[o].im);
+  csync<NW>();
+  // eps - U on the diagonal, formed in FP64 and rounded once
+  for (int r = tid; r < b; r += NT)
+    out[r * b + r] = out[r * b + r] + mk((T)(eps.re - D.U[l * rpb + r / spr]), (T)eps.im);
   csync<NW>();
   for (int side = 0; side < 2; ++side) {
     if ((side == 0 && l != 0) || (side == 1 && l != L - 1)) continue;
@@ -616,11 +643,12 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
     cx<T>* Rn = CMP ? V0 : V1;
     const long long lstride = (long long)(bb + (real ? bm : 0)) * sizeof(cx<T>);
     float gmax = 0.0f;   // largest |gL_l entry|^2 of this thread (growth diagnostic)
+    float gdg = 0.0f;
     for (int l = 0; l < L; ++l) {
       if (l > 0) {
         const int* ccnt = C.cs_cnt + (long long)(l - 1) * b;
         const int* cidx = C.cs_idx + (long long)(l - 1) * b * kmax;
-        const cd* cval = C.cs_val + (long long)(l - 1) * b * kmax;
+        const cx<T>* cval = csval_t<T>(C) + (long long)(l - 1) * b * kmax;
         hdn_times<T, NT>(X, P, b, b, b, ccnt, cidx, cval, kmax, tid);            // X = H_{l,l-1} gL_{l-1}
         csync<NW>();
         times_hup<T, NT>(A, X, b, b, ccnt, cidx, cval, kmax, tid);               // y_l = X H_{l-1,l}
@@ -649,10 +677,10 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
         alpha_minus<T, NW>(A, nullptr, 0, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);
       }
       binv<T, NW>(A, b, col, perm, redf, redi, tid);
-      if (!TWO && C.sym) {
-        symmetrize<T, NT>(A, b, tid);
-        csync<NW>();
-      }
+      if (!TWO && C.sym)   // largest |gL_l diagonal|^2 seen by this thread (symmetric-update gate)
+        for (int r = tid; r < b; r += NT)
+          gdg = fmaxf(gdg, fmaf((float)A[r * b + r].re, (float)A[r * b + r].re,
+                                (float)A[r * b + r].im * (float)A[r * b + r].im));
       // stage gL_l (and R_l)
       cx<T>* sg = reinterpret_cast<cx<T>*>(stage + (long long)l * lstride);
       for (int o = tid; o < nn; o += NT) {
@@ -672,6 +700,14 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
       }
     }
 
+    // The symmetric form of the G_ll update is used for a lane only while every gL_l stays
+    // moderate.  Near a bound state of the half chain [0, l] (a pole of gL_l broadened by eta
+    // only) the Dyson update cancels terms of size |gL|^2 / |G|, and the mirrored form then
+    // turns the rounding asymmetry of gL_l into errors of order one; those lanes take the
+    // general update.
+    const bool lsym = !TWO && C.sym && cta_max<NW>((double)gdg, redd, tid) <= SYM_GL_MAX * SYM_GL_MAX;
+    if (a.lane_stats && tid == 0) atomicAdd(a.lane_stats + (real ? 0 : 2) + (lsym ? 0 : 1), 1ull);
+
     // ---- backward sweep
     //  Dyson variant:     G (P: gL_{L-1} = G_{L-1,L-1}), Gl, Z, Wm
     //  two-sided variant: G, Gr = gR_{l+1}, Wk, W1, GlB = gL_l, GpB = gL_{l-1}
@@ -684,6 +720,10 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
     cx<T>* Wm = M3;      // Dyson: Wm;    two-sided: Gr
     cx<T>* GlB = M4;     // two-sided only
     cx<T>* GpB = M5;     // two-sided only
+    if (lsym) {
+      symmetrize<T, NT>(G, b, tid);
+      csync<NW>();
+    }
     // compact: K takes V0, R_l lives in the Gl buffer (loaded after each G_ll update)
     cx<T>* K = CMP ? V0 : ((R == V0) ? V1 : V0);
     cx<T>* Kn = CMP ? K : V2;
@@ -713,18 +753,22 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
       for (int o = tid; o < nn; o += NT) GlB[o] = sg[o];
       csync<NW>();
     }
-    double rnum = 0.0, rden = 0.0;   // sum-rule residual: max(0, A_S + A_D + 2 Im G) / max |2 Im G|
+    T rnum = T(0), rden = T(0);   // sum-rule residual: max(0, A_S + A_D + 2 Im G) / max |2 Im G|
     for (int l = L - 1; l >= 0; --l) {
       if (l < L - 1) {
         const cx<T>* sg = reinterpret_cast<const cx<T>*>(stage + (long long)l * lstride);
         const int* ccnt = C.cs_cnt + (long long)l * b;
         const int* cidx = C.cs_idx + (long long)l * b * kmax;
-        const cd* cval = C.cs_val + (long long)l * b * kmax;
+        const cx<T>* cval = csval_t<T>(C) + (long long)l * b * kmax;
         if (!TWO) {
           for (int o = tid; o < nn; o += NT) Gl[o] = sg[o];
           if (real && !CMP)
             for (int o = tid; o < b * mS; o += NT) Rl[o] = sg[bb + o];
           csync<NW>();
+          if (lsym) {   // the symmetric update needs gL_l symmetric to the last bit
+            symmetrize<T, NT>(Gl, b, tid);
+            csync<NW>();
+          }
           times_hup<T, NT>(Z, Gl, b, b, ccnt, cidx, cval, kmax, tid);                // Z = gL_l H_{l,l+1}
           csync<NW>();
           if constexpr (CMP) {
@@ -737,7 +781,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
               store_r<T, NT>(K, mD, rt, b, mD, tid);
             }
             csync<NW>();
-            if (C.sym) {
+            if (lsym) {
               // G_ll = gL_l + Z G_{l+1} Z^T is symmetric: upper triangle, mirrored
               bgemm_symt_r<T, NT>(rt, G, Z, Gl, b, tid);
               csync<NW>();
@@ -756,7 +800,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
             if (real) bgemm<T, NT>(Kn, mD, Z, b, K, mD, b, b, mD, nullptr, 0, tid);  // K_l = Z K_{l+1}
             bgemm<T, NT>(Wm, b, Z, b, G, b, b, b, b, nullptr, 0, tid);               // Wm = Z G_{l+1}
             csync<NW>();
-            if (C.sym) {
+            if (lsym) {
               bgemm_symt<T, NT>(G, Wm, Z, Gl, b, tid);                                // gL_l + Wm Z^T
             } else {
               hdn_times<T, NT>(Z, Gl, b, b, b, ccnt, cidx, cval, kmax, tid);         // Z = H_{l+1,l} gL_l
@@ -773,7 +817,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
           cx<T>* Gr = Wm;
           const int* rcnt = C.rs_cnt + (long long)l * b;
           const int* ridx = C.rs_idx + (long long)l * b * kmax;
-          const cd* rval = C.rs_val + (long long)l * b * kmax;
+          const cx<T>* rval = rsval_t<T>(C) + (long long)l * b * kmax;
           if (real)
             for (int o = tid; o < b * mS; o += NT) Rl[o] = sg[bb + o];
           if (l > 0) {
@@ -790,7 +834,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
           if (l > 0) {
             const int* pcnt = C.cs_cnt + (long long)(l - 1) * b;
             const int* pidx = C.cs_idx + (long long)(l - 1) * b * kmax;
-            const cd* pval = C.cs_val + (long long)(l - 1) * b * kmax;
+            const cx<T>* pval = csval_t<T>(C) + (long long)(l - 1) * b * kmax;
             hdn_times<T, NT>(W1, GpB, b, b, b, pcnt, pidx, pval, kmax, tid);          // H_{l,l-1} gL_{l-1}
             csync<NW>();
             times_hup<T, NT>(Wk, W1, b, b, pcnt, pidx, pval, kmax, tid);              // y_l
@@ -826,9 +870,9 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
             for (int j = 0; j < mD; ++j) ad = fma(K[r * mD + j].im, K[r * mD + j].im, fma(K[r * mD + j].re, K[r * mD + j].re, ad));
             vr[r / spr] += wS * (double)as + wD * (double)ad;
             if (a.resid) {
-              const double gim = (double)G[r * b + r].im;
-              rnum = fmax(rnum, (double)as + (double)ad + 2.0 * gim);
-              rden = fmax(rden, fabs(2.0 * gim));
+              const T gim2 = T(2) * G[r * b + r].im;
+              rnum = fmax(rnum, as + ad + gim2);
+              rden = fmax(rden, fabs(gim2));
             }
           }
       } else if (tid < 32) {
@@ -861,8 +905,8 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
       const double Tval = tid < 32 ? wsum(tv) : 0.0;
       if (tid == 0) a.Tpart[W.tout] = Tval;
       if (a.resid) {
-        const double rn = cta_max<NW>(rnum, redd, tid);
-        const double rd = cta_max<NW>(rden, redd, tid);
+        const double rn = cta_max<NW>((double)rnum, redd, tid);
+        const double rd = cta_max<NW>((double)rden, redd, tid);
         if (tid == 0) a.resid[W.tout] = rn / fmax(rd, 1e-300);
       }
       if (a.growth) {

@@ -25,7 +25,7 @@ class Opts(C.Structure):
     _fields_ = [("device_ordinal", C.c_int), ("stream", C.c_void_p), ("hbm_budget_bytes", C.c_size_t),
                 ("precision", C.c_int), ("flag_threshold", C.c_double), ("edge_window", C.c_double),
                 ("fault_alloc_after", C.c_int), ("growth_threshold", C.c_double), ("blk_warps", C.c_int),
-                ("blk_ctas_per_sm", C.c_int)]
+                ("blk_ctas_per_sm", C.c_int), ("general_update", C.c_int)]
 
 
 class Lead(C.Structure):
@@ -108,6 +108,7 @@ _PROTOS = {
     "negf_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "negf_kernel_time": (C.c_int, [C.c_void_p, _dp, C.POINTER(C.c_uint64)]),
     "negf_fp64_peak": (C.c_int, [C.c_void_p, _dp]),
+    "negf_sweep_lanes": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "negf_blk_width": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, _ip, _ip]),
     "negf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)]),
     "negf_serve_step": (C.c_int, [C.c_void_p, _ip]),
@@ -195,10 +196,11 @@ class Context:
     """One libnegf context (negf_create / negf_destroy)."""
 
     def __init__(self, device=0, stream=None, hbm_budget=0, precision=PREC_FP64, flag_threshold=0.0,
-                 edge_window=0.0, fault_alloc_after=0, growth_threshold=0.0, blk_warps=0, blk_ctas_per_sm=0):
+                 edge_window=0.0, fault_alloc_after=0, growth_threshold=0.0, blk_warps=0, blk_ctas_per_sm=0,
+                 general_update=0):
         self.lib = load()
         o = Opts(device, stream or 0, hbm_budget, precision, flag_threshold, edge_window, fault_alloc_after,
-                 growth_threshold, blk_warps, blk_ctas_per_sm)
+                 growth_threshold, blk_warps, blk_ctas_per_sm, general_update)
         h = C.c_void_p()
         rc = self.lib.negf_create(C.byref(h), C.byref(o))
         if rc:
@@ -416,6 +418,13 @@ class Context:
         n = C.c_uint64()
         self._chk(self.lib.negf_kernel_time(self.h, C.byref(ms), C.byref(n)))
         return ms.value, n.value
+
+    def sweep_lanes(self):
+        """Lanes of the wide-block sweep since the last call, by update form:
+        (real symmetric, real general, contour symmetric, contour general)."""
+        v = (C.c_uint64 * 4)()
+        self._chk(self.lib.negf_sweep_lanes(self.h, v))
+        return tuple(int(x) for x in v)
 
     def fp64_peak(self):
         t = C.c_double()

@@ -95,6 +95,26 @@ def test_flux_threaded_tube_general_blocks(n_tube, N, blk_warps):
     check(p, r, o)
 
 
+@pytest.mark.parametrize("N,n_real", [(64, 96), (192, 512)])
+def test_symmetric_update_with_bound_states(N, n_real):
+    """A potential well deep enough to hold states in the gap: lanes near those states have a
+    nearly singular half-chain gL_l and must take the general update.  The default run (the
+    symmetric update where it is safe) must match the general update and, for the shorter
+    channel, the oracle."""
+    from paper_2407_14633_gb300 import negf
+    i = np.arange(N)
+    U = -0.1 * i / (N - 1) - 0.35 * np.exp(-((i - 0.5 * N) / (0.08 * N)) ** 2)
+    p = case_params("real", N, n_real, 16, U, mu_D=-0.1, n_tube=17, U_S=0.0, U_D=-0.1)
+    out = []
+    for gen in (0, 1):
+        with negf.Context(general_update=gen) as c2:
+            _, r = run_lib(c2, p)
+            out.append(r)
+    check(p, out[0], out[1])
+    if N <= 64:
+        check(p, out[0], run_oracle(p, chunk=16))
+
+
 def ogr_grid(p):
     from tests.cases import oracle_grid
     return oracle_grid(p)

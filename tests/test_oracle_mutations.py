@@ -1,0 +1,142 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in a copy of an oracle module's source (a dropped term, a
+swapped operand, a flipped sign or the wrong root), loads the copy as a throw-away module of
+the oracle package, and checks that a pin which the real module passes rejects the copy.
+The real oracle is never modified."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import green as gr
+from oracle import leads as ld
+from oracle import model as mdl
+from oracle import quadrature as qd
+
+T_HOP = -2.7
+ORACLE_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
+
+
+def mutant(module, old, new):
+    """The oracle module `module` with the source text `old` replaced once by `new`."""
+    path = os.path.join(ORACLE_DIR, module + ".py")
+    with open(path) as f:
+        src = f.read()
+    assert src.count(old) == 1, "mutation site not found in oracle/%s.py: %r" % (module, old)
+    ns = {"__name__": "oracle._mutant_" + module, "__package__": "oracle", "__file__": path}
+    exec(compile(src.replace(old, new), path, "exec"), ns)
+    return ns
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def recursion_vs_dense(rgf):
+    """Largest relative gap of (G_ll, A_S, A_D, T) between `rgf` and the dense inverse."""
+    chain = mdl.realspace_chain(5, T_HOP, 6, 0.0, -0.1)
+    # site disorder inside the rings breaks the rotation symmetry of the tube, under which
+    # H_{l,l+1} and its transpose would give the same recursion
+    rng = np.random.default_rng(11)
+    chain.Hdiag = chain.Hdiag + np.array([np.diag(rng.uniform(-0.3, 0.3, 5)) for _ in range(6)])
+    U = 0.05 * np.sin(np.arange(6)) + np.linspace(0, -0.1, 6)
+    eps = np.array([-2.1, -0.9, -0.3, 0.27, 0.8, 1.7]) + 1e-6j
+    d = gr.dense_lanes(chain, U, eps)
+    r = rgf(chain, U, eps)
+    return max(rel(r["Gdiag"], d["Gdiag"]), rel(r["AS"], d["AS"]), rel(r["AD"], d["AD"]),
+               np.max(np.abs(r["T"] - d["T"])) / max(1.0, np.max(np.abs(d["T"]))))
+
+
+GREEN_MUTATIONS = [
+    ("left-connected term with swapped couplings",
+     "y[l] = Hdn[l - 1] @ gL[l - 1] @ Hup[l - 1]", "y[l] = Hup[l - 1] @ gL[l - 1] @ Hdn[l - 1]"),
+    ("dropped left-connected term in G_ll", "Gll = inv(alpha - x - y)", "Gll = inv(alpha - x)"),
+    ("drain column propagated with gR", "colN[l - 1] = gL[l - 1] @ Hup[l - 1] @ colN[l]",
+     "colN[l - 1] = gR[l - 1] @ Hup[l - 1] @ colN[l]"),
+    ("source spectral function with the drain Gamma", "AS = col0 @ gS[None] @ _dag(col0)",
+     "AS = col0 @ gD[None] @ _dag(col0)"),
+]
+
+
+def test_real_recursion_passes_its_pin():
+    assert recursion_vs_dense(gr.rgf_lanes) < 1e-11
+
+
+@pytest.mark.parametrize("name,old,new", GREEN_MUTATIONS)
+def test_recursion_pin_rejects(name, old, new):
+    m = mutant("green", old, new)
+    assert recursion_vs_dense(m["rgf_lanes"]) > 1e-6, name
+
+
+def retarded_root_gap(surface_gf):
+    """Largest violation of Im g <= 0 and of the defining recursion over a grid of dimer leads."""
+    worst = 0.0
+    for a1, a2 in ((7.29, 1.0), (1.0, 7.29), (3.0, 3.0), (7.29, 20.0)):
+        eps = np.linspace(-6, 6, 241) + 1e-3j
+        g = surface_gf(eps, a1, a2)
+        worst = max(worst, float(np.max(g.imag)))
+        # g = 1 / (eps - a1 / (eps - a2 g)) for the dimerised chain
+        res = g - 1.0 / (eps - a1 / (eps - a2 * g))
+        worst = max(worst, float(np.max(np.abs(res))))
+    return worst
+
+
+def test_real_surface_gf_passes_its_pin():
+    assert retarded_root_gap(ld.surface_gf_dimer) < 1e-9
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("advanced root picked", "pick_imag = np.where(g1.imag < g2.imag, g1, g2)",
+     "pick_imag = np.where(g1.imag > g2.imag, g1, g2)"),
+    ("wrong quadratic root formula", "g2 = 2.0 * e / q", "g2 = 2.0 * e * q"),
+])
+def test_surface_gf_pin_rejects(name, old, new):
+    m = mutant("leads", old, new)
+    assert retarded_root_gap(m["surface_gf_dimer"]) > 1e-3, name
+
+
+def gl_exactness_gap(gauss_legendre):
+    x, w = gauss_legendre(12)
+    worst = 0.0
+    for k in range(24):
+        exact = 0.0 if k % 2 else 2.0 / (k + 1)
+        worst = max(worst, abs(float(np.sum(w * x ** k)) - exact))
+    return worst
+
+
+def test_real_gauss_legendre_passes_its_pin():
+    assert gl_exactness_gap(qd.gauss_legendre) < 1e-13
+
+
+def test_gauss_legendre_pin_rejects_a_wrong_weight():
+    src = open(os.path.join(ORACLE_DIR, "quadrature.py")).read()
+    # the weights are 2 / ((1 - x^2) P_n'(x)^2); dropping the 2 halves every weight
+    old = [ln for ln in src.splitlines() if "2.0 / ((1.0 - x * x)" in ln or "2.0 / ((1 - x * x)" in ln]
+    assert len(old) == 1, "weight formula not found in oracle/quadrature.py"
+    m = mutant("quadrature", old[0], old[0].replace("2.0 / ((1", "1.0 / ((1", 1))
+    assert gl_exactness_gap(m["gauss_legendre"]) > 1e-3
+
+
+def half_filling_gap(charge_mod):
+    dev = mdl.cnt_build("mode", 17, T_HOP, 10, 0.0, 0.0, modes=(6,))
+    n0 = charge_mod["neutral_charge"](dev, 48, -9.5) if isinstance(charge_mod, dict) else \
+        charge_mod.neutral_charge(dev, 48, -9.5)
+    # g_s g_b / 2 = 2 electrons per site of a mode chain at half filling
+    return float(np.max(np.abs(n0 - 2.0)))
+
+
+def test_real_charge_passes_half_filling():
+    from oracle import charge as ch
+    assert half_filling_gap(ch) < 1e-9
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("contour term with the wrong sign", "g / np.pi", "-g / np.pi"),
+])
+def test_half_filling_pin_rejects(name, old, new):
+    src = open(os.path.join(ORACLE_DIR, "charge.py")).read()
+    if src.count(old) != 1:
+        pytest.fail("mutation site %r not found once in oracle/charge.py" % old)
+    m = mutant("charge", old, new)
+    assert half_filling_gap(m) > 0.1, name
