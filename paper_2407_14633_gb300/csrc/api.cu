@@ -86,7 +86,7 @@ Dev* get_dev(Ctx* c, int dev) {
 void free_dev(Ctx* c, Dev* d) {
   for (auto& ch : d->ch) {
     for (DBuf* b : {&ch.dHdiag, &ch.dHup, &ch.dcs_cnt, &ch.dcs_idx, &ch.dcs_val, &ch.drs_cnt, &ch.drs_idx,
-                    &ch.drs_val, &ch.dhsq, &ch.dHdiag_f, &ch.dcs_val_f, &ch.drs_val_f})
+                    &ch.drs_val, &ch.dhsq, &ch.dHdiag_f, &ch.dcs_val_f, &ch.drs_val_f, &ch.dhsq_f})
       c->arena.release(*b);
     for (int s = 0; s < 2; ++s)
       for (DBuf* b : {&ch.da1[s], &ch.da2[s], &ch.dat[s], &ch.dsites[s], &ch.dtw[s]})
@@ -244,6 +244,10 @@ int upload_chain(Ctx* c, Dev* d, ChainData& ch) {
   std::vector<double> hsq(nl, 0.0);
   if (b == 1)
     for (int l = 0; l < L - 1; ++l) hsq[l] = ch.Hup[2 * l] * ch.Hup[2 * l] + ch.Hup[2 * l + 1] * ch.Hup[2 * l + 1];
+  ch.diag_real = true;
+  for (size_t i = 1; i < ch.Hdiag.size(); i += 2) ch.diag_real = ch.diag_real && ch.Hdiag[i] == 0.0;
+  std::vector<float> hsq_f(hsq.begin(), hsq.end());
+  if ((rc = upload(c, ch.dhsq_f, hsq_f.data(), hsq_f.size() * 4))) return rc;
   return upload(c, ch.dhsq, hsq.data(), hsq.size() * 8);
 }
 

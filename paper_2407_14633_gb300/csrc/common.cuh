@@ -110,6 +110,12 @@ struct ChainView {
   const cf* cs_val_f;
   const cf* rs_val_f;
   const double* hsq; // block 1: |H_{l,l+1}|^2 per layer (L-1)
+  const float* hsq_f; // its FP32 copy
+  // block 1: Re H_ll + U_l per layer for this launch (FP64 and FP32), formed once per launch
+  // by prep_kernel; null where the sweep forms it itself.  diag_real: Im H_ll = 0 everywhere.
+  const double* hu;
+  const float* hu_f;
+  int diag_real;
   double g_b;
   int sym;           // real H blocks and real lead rows: every G_ll is complex symmetric
   LeadView lead[2];
@@ -198,6 +204,16 @@ struct ReduceDev {
   double* I;
 };
 int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s);
+
+// Per-launch layer diagonals of the 1 x 1 chains: hu[l] = Re H_ll + U_l, hu_f its FP32 copy.
+struct PrepDesc {
+  int L;
+  const cd* Hdiag;
+  const double* U;
+  double* hu;
+  float* hu_f;
+};
+int launch_prep(const PrepDesc* descs, int n, int max_L, cudaStream_t s);
 
 // per-layer potential added to diagonal blocks is applied inside the sweep kernels.
 

@@ -76,6 +76,10 @@ DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
     cv.cs_val_f = (const cf*)ch.dcs_val_f.p;
     cv.rs_val_f = (const cf*)ch.drs_val_f.p;
     cv.hsq = (const double*)ch.dhsq.p;
+    cv.hsq_f = (const float*)ch.dhsq_f.p;
+    cv.diag_real = ch.diag_real ? 1 : 0;
+    cv.hu = nullptr;   // set by build_plan for 1 x 1 chains
+    cv.hu_f = nullptr;
     cv.g_b = ch.g_b;
     // complex symmetric Green's functions: real symmetric H blocks, real couplings and leads
     // whose circulant couplings have real first rows (their Sigma is then symmetric)
@@ -113,7 +117,7 @@ int check_ready(Ctx* c, Dev* d) {
 // reset, sweeps, second stage), so it can be captured in a CUDA graph and replayed.
 void free_plan_bufs(Ctx* c, PlanBufs& b) {
   for (DBuf* x : {&b.views, &b.items, &b.order, &b.counter, &b.partial, &b.tpart, &b.stage, &b.reduce, &b.status,
-                  &b.resid, &b.order2, &b.growth})
+                  &b.resid, &b.order2, &b.growth, &b.prep, &b.hu})
     c->arena.release(*x);
 }
 
@@ -431,6 +435,18 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       }
     }
 
+  // layer diagonals of the 1 x 1 chains, formed once per launch by prep_kernel
+  long long hu_elems = 0;
+  int n_prep = 0, prep_L = 0;
+  for (int di = 0; di < nd; ++di)
+    if (devs[di]->block == 1) {
+      hu_elems += (long long)devs[di]->n_chains * P.views[di].L;
+      n_prep += devs[di]->n_chains;
+      prep_L = std::max(prep_L, P.views[di].L);
+    }
+  const size_t hu_bytes = (size_t)std::max<long long>(hu_elems * 12, 16);
+  const size_t prep_bytes = std::max<size_t>(sizeof(PrepDesc) * n_prep, 16);
+
   // Under an HBM budget the staging of the forward sweep (per resident warp / CTA) is what
   // adapts: resident CTAs are capped so that it fits beside everything else.
   if (c->arena.budget) {
@@ -441,7 +457,8 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     long long other = extra(B.views, sizeof(DeviceView) * nd) + extra(B.items, sizeof(WorkItem) * n_items) +
                       extra(B.order, sizeof(int) * n_items) + extra(B.partial, sizeof(double) * std::max<long long>(part, 1)) +
                       extra(B.tpart, sizeof(double) * std::max<long long>(tpos, 1)) + extra(B.reduce, sizeof(ReduceDev) * nd) +
-                      extra(B.counter, sizeof(int) * 16) + extra(B.status, sizeof(int));
+                      extra(B.counter, sizeof(int) * 16) + extra(B.status, sizeof(int)) + extra(B.hu, hu_bytes) +
+                      extra(B.prep, prep_bytes);
     if (P.prec != NEGF_PREC_FP64)
       other += extra(B.resid, sizeof(double) * tpos) + extra(B.growth, sizeof(double) * tpos) + extra(B.order2, sizeof(int) * n_items);
     for (int di = 0; di < nd; ++di) {
@@ -471,6 +488,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       !ensure(c, B.tpart, sizeof(double) * std::max<long long>(tpos, 1)) ||
       !ensure(c, B.stage, (size_t)std::max<long long>(stage_bytes, 16)) ||
       !ensure(c, B.reduce, sizeof(ReduceDev) * nd) || !ensure(c, B.status, sizeof(int)) ||
+      !ensure(c, B.hu, hu_bytes) || !ensure(c, B.prep, prep_bytes) ||
       (P.prec != NEGF_PREC_FP64 && (!ensure(c, B.resid, sizeof(double) * std::max<long long>(tpos, 1)) ||
                                     !ensure(c, B.growth, sizeof(double) * std::max<long long>(tpos, 1)) ||
                                     !ensure(c, B.order2, sizeof(int) * n_items))))
@@ -507,8 +525,33 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     R.T = (double*)d->dT.p;
     R.I = (double*)d->dI.p;
   }
+  std::vector<PrepDesc> prep;
+  {
+    double* hud = (double*)B.hu.p;
+    float* huf = (float*)(hud + hu_elems);
+    long long off = 0;
+    for (int di = 0; di < nd; ++di) {
+      if (devs[di]->block != 1) continue;
+      DeviceView& v = P.views[di];
+      for (int ch = 0; ch < v.n_chains; ++ch) {
+        PrepDesc q;
+        q.L = v.L;
+        q.Hdiag = v.ch[ch].Hdiag;
+        q.U = v.U;
+        q.hu = hud + off;
+        q.hu_f = huf + off;
+        v.ch[ch].hu = q.hu;
+        v.ch[ch].hu_f = q.hu_f;
+        prep.push_back(q);
+        off += v.L;
+      }
+    }
+  }
+  P.n_prep = n_prep;
+  P.prep_L = prep_L;
   // synchronous uploads: the host vectors die with this call
   if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+      (n_prep && cudaMemcpy(B.prep.p, prep.data(), sizeof(PrepDesc) * n_prep, cudaMemcpyHostToDevice)) ||
       cudaMemcpy(B.views.p, P.views.data(), sizeof(DeviceView) * nd, cudaMemcpyHostToDevice) ||
       cudaMemcpy(B.items.p, items.data(), sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice) ||
       cudaMemcpy(B.order.p, order_all.data(), sizeof(int) * n_items, cudaMemcpyHostToDevice) ||
@@ -606,6 +649,10 @@ int launch_plan(Ctx* c, Plan& P) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
+  }
+  if (P.n_prep) {
+    if (launch_prep((const PrepDesc*)B.prep.p, P.n_prep, P.prep_L, s)) return set_err(c, NEGF_ECUDA, "prep launch failed");
+    ++c->launches;
   }
   for (int g = 0; g < NGROUPS; ++g) {
     if (!P.ncls[g]) continue;

@@ -48,7 +48,8 @@ struct ChainData {
   HostLead lead[2];
   // device copies
   DBuf dHdiag, dHup, dcs_cnt, dcs_idx, dcs_val, drs_cnt, drs_idx, drs_val, dhsq;
-  DBuf dHdiag_f, dcs_val_f, drs_val_f;   // complex64 copies for the complex64 sweeps
+  DBuf dHdiag_f, dcs_val_f, drs_val_f, dhsq_f;   // FP32 copies for the complex64 sweeps
+  bool diag_real = false;                        // Im H_ll = 0 everywhere
   DBuf da1[2], da2[2], dat[2], dsites[2], dtw[2];
   int kmax = 0;
 };
@@ -58,6 +59,7 @@ struct ChainData {
 // later call reallocated.
 struct PlanBufs {
   DBuf views, items, order, counter, partial, tpart, stage, reduce, status, resid, order2, growth;
+  DBuf prep, hu;   // layer diagonals of the 1 x 1 chains (descriptors, values)
 };
 
 struct ScSession;
@@ -152,6 +154,7 @@ struct Plan {
   std::vector<double> growth;             // per T slot
   int recomputed = 0;
   bool want_diag = false;
+  int n_prep = 0, prep_L = 0;             // prep_kernel descriptors and longest chain
 };
 int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOverride>* ov, int chain_only,
                Plan& P, PlanBufs* bufs = nullptr);

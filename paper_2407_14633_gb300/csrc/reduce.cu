@@ -2,7 +2,10 @@
 // sum the per-item partial ring sums in item order (deterministic, independent of the
 // schedule and of the rest of the batch), sum T(E) over chains with their band
 // degeneracy, and reduce the Landauer current I = g_s (e^2/h) sum_k w_k T_k (fS_k - fD_k)
-// with a fixed-shape tree in shared memory.
+// with a fixed-shape tree in shared memory.  Also the per-launch layer diagonals of the 1 x 1
+// chains (prep_kernel), which the sweep would otherwise form in every lane.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace negf {
@@ -47,6 +50,24 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReduceDev* devs) {
 
 int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s) {
   reduce_kernel<<<n_devs, 256, 0, s>>>(devs);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+__global__ void prep_kernel(const PrepDesc* descs, int n) {
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const PrepDesc q = descs[i];
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < q.L; l += gridDim.x * blockDim.x) {
+      const double v = q.Hdiag[l].re + q.U[l];
+      q.hu[l] = v;
+      q.hu_f[l] = (float)v;
+    }
+  }
+}
+
+int launch_prep(const PrepDesc* descs, int n, int max_L, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const dim3 grid((unsigned)std::min((max_L + 255) / 256, 64), (unsigned)std::min(n, 65535));
+  prep_kernel<<<grid, 256, 0, s>>>(descs, n);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

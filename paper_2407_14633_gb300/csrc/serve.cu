@@ -98,6 +98,7 @@ size_t request_bytes(const Req& r) {
   b += C * (N * 16 * 2 + N * 8 + N * 64);     // blocks, |h|^2, sparse form
   b += N * 8 * 4 + nr * 8 * 5 + nc * 32;      // U, outputs, grid
   b += items * N * 8 + C * nr * 8;            // partial sums, T partials
+  b += C * N * 12 + C * 64;                   // per-launch layer diagonals and their descriptors
   b += 2 * M * N * 8 + 6 * N * 8 + M * 8;     // Broyden state
   return b;
 }
@@ -232,7 +233,8 @@ int step_locked(Ctx* c, Serve* s, int* n_active) {
     size_t Lmax = r->N;
     for (Req* q : s->active) Lmax = std::max<size_t>(Lmax, q->N);
     const size_t stage_min = Lmax * 8 * 5 * 32 * 8;
-    if (budget && !s->active.empty() && s->active_bytes + need + stage_min > budget) break;
+    const size_t margin = 1 << 20;   // plan descriptors, counters, allocation rounding
+    if (budget && !s->active.empty() && s->active_bytes + need + stage_min + margin > budget) break;
     if (budget && !released) {
       // the batch plan is rebuilt after admission anyway; its staging is released first so
       // the set-up of the new request (its neutral charge) has room for its own sweep

@@ -48,6 +48,20 @@ __device__ __forceinline__ cx<T> ld_c(const unsigned char* p) {
 }  // namespace
 
 // ------------------------------------------------------------------ b = 1
+// the FP64 or FP32 copy of a per-layer array
+template <typename T>
+__device__ __forceinline__ const T* pick(const double* d, const float* f);
+template <>
+__device__ __forceinline__ const double* pick<double>(const double* d, const float* f) {
+  (void)f;
+  return d;
+}
+template <>
+__device__ __forceinline__ const float* pick<float>(const double* d, const float* f) {
+  (void)d;
+  return f;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
   extern __shared__ double sm_b1[];
@@ -91,7 +105,8 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
     const cx<T> SS = mk((T)sS.re, (T)sS.im), SD = mk((T)sD.re, (T)sD.im);
     const double* U = D.U;
     const cd* Hd = C.Hdiag;
-    const double* hsq = C.hsq;
+    const T* hsq = pick<T>(C.hsq, C.hsq_f);
+    const T* hu = pick<T>(C.hu, C.hu_f);   // Re H_ll + U_l of this launch (may be null)
 
     // ---------------- forward sweep
     cx<T> gl = mk(T(0), T(0));
@@ -102,27 +117,34 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
     T rmaxg = T(0);           // largest |gL_l|^2 (growth diagnostic)
     const int nf = (W.kind == 0) ? (want_r ? 5 : 4) : 2;
     for (int l = 0; l < L; ++l) {
-      const cd h = Hd[l];
-      cx<T> x = mk((T)(eps.re - h.re - U[l]), (T)(eps.im - h.im));
-      (void)e;
+      cx<T> x;
+      if (hu) {
+        x.re = e.re - hu[l];
+        x.im = C.diag_real ? e.im : (T)(eps.im - Hd[l].im);
+      } else {
+        const cd h = Hd[l];
+        x = mk((T)(eps.re - h.re - U[l]), (T)(eps.im - h.im));
+      }
       if (l == 0) x = x - SS;
       if (l == L - 1) x = x - SD;
+      T p = T(0);               // |h_{l-1,l}|^2 |gL_{l-1}|^2
       if (l > 0) {
-        const T hs = (T)hsq[l - 1];
+        const T hs = hsq[l - 1];
         x.re = fma(-hs, gl.re, x.re);
         x.im = fma(-hs, gl.im, x.im);
-        if (W.kind == 0) ql = hs * rl * ql;
-        if (want_r) qu = hs * rl * qu;
+        p = hs * rl;
+        if (W.kind == 0) ql = p * ql;
+        if (want_r) qu = p * qu;
       }
       const T r = T(1) / fma(x.re, x.re, x.im * x.im);
       gl = mk(x.re * r, -x.im * r);
       rl = r;
-      rmaxg = r > rmaxg ? r : rmaxg;
+      if (a.growth) rmaxg = r > rmaxg ? r : rmaxg;
       T* s = st + (long long)l * nf * 32;
       s[lane] = gl.re;
       s[32 + lane] = gl.im;
       if (W.kind == 0) {
-        s[64 + lane] = r;
+        s[64 + lane] = p;       // used by the backward step at layer l - 1
         s[96 + lane] = ql;
         if (want_r) s[128 + lane] = qu;
       }
@@ -133,19 +155,22 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
     T c = abs2(G);            // |G_{l,L-1}|^2
     // sum-rule residual of the lane: max(0, max_l (A_S + A_D + 2 Im G)_ll) / max_l |2 Im G_ll|
     double rnum = 0.0, rden = 0.0;
+    const double wDg = wD * gamD;
+    T pn = T(0);              // |h_{l,l+1}|^2 |gL_l|^2, read one layer ahead
     for (int l = L - 1; l >= 0; --l) {
       const T* s = st + (long long)l * nf * 32;
       if (l < L - 1) {
         const cx<T> gll = mk(s[lane], s[32 + lane]);
-        const T hs = (T)hsq[l];
+        const T hs = hsq[l];
         cx<T> t = scale(gll * G, hs);        // |h|^2 gL G_{l+1}
         G = cmac(gll, gll, t);               // gL + gL (|h|^2 gL G_{l+1})
-        if (W.kind == 0) c = s[64 + lane] * hs * c;
+        if (W.kind == 0) c = pn * c;         // |G_{l,L-1}|^2
       }
+      if (W.kind == 0) pn = s[64 + lane];
       double v;
       if (W.kind == 0) {
         const T q = s[96 + lane];
-        v = (double)(q * abs2(G)) + wD * gamD * (double)c;
+        v = fma(wDg, (double)c, (double)(q * abs2(G)));
         if (want_r) {
           // A_S + A_D + 2 Im G <= 0 up to rounding (equality up to 2 eta |G|^2 terms)
           const double as = gamS * (double)s[128 + lane] * (double)abs2(G);
