@@ -173,6 +173,17 @@ static int blk_occ(Ctx* c, bool f32, int w, int b, int m) {
   return occ;
 }
 
+// CTA width for a group of n lanes: the widest whose resident CTAs still hold every lane at
+// once, so that a few lanes are spread over the warps of otherwise idle SMs (the arithmetic
+// does not depend on the width); 0 when no width holds them all in one wave.
+static int partial_wave_width(Ctx* c, bool f32, int b, int m, int n) {
+  for (int w : {4, 2, 1}) {
+    const int occ = blk_occ(c, f32, w, b, m);
+    if (occ > 0 && (long long)n <= (long long)c->sms * occ) return w;
+  }
+  return 0;
+}
+
 // Autotuner of the wide-block sweep's launch shape: CTA width (1, 2, 4 warps) and resident
 // CTAs per SM.  Every output element and every reduction of that kernel has an evaluation
 // order that depends on neither, so the choice changes speed only.  The candidates are, per
@@ -377,8 +388,11 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       if (it != c->blk_tuned.end()) {
         P.gw[g] = it->second.first;
         P.gcap[g] = it->second.second;
-      } else {
-        tune_g[g] = P.ncls[g] >= c->sms && capst == cudaStreamCaptureStatusNone;
+      } else if (P.ncls[g] >= c->sms && capst == cudaStreamCaptureStatusNone) {
+        tune_g[g] = true;
+      } else if (P.ncls[g] < c->sms) {
+        const int w = partial_wave_width(c, group_f32(g), P.gb[g], P.gm[g], P.ncls[g]);
+        if (w) P.gw[g] = w;
       }
     }
   }
@@ -566,7 +580,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
 }
 
 static int launch_group(Ctx* c, const Plan& P, int g, const int* order, int n, int grid, double* resid,
-                        double* growth) {
+                        double* growth, int warps = 0) {
   const int cls = group_class(g);
   const bool f32 = group_f32(g);
   SweepArgs a = group_args(P, g, order, n, resid, growth);
@@ -578,7 +592,7 @@ static int launch_group(Ctx* c, const Plan& P, int g, const int* order, int n, i
   else if (cls == 1)
     rc = f32 ? launch_sweep_b2_f32(a, grid, P.block_threads, s) : launch_sweep_b2_f64(a, grid, P.block_threads, s);
   else
-    rc = launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], grid, P.gw[g], s);
+    rc = launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], grid, warps > 0 ? warps : P.gw[g], s);
   if (rc) return set_err(c, NEGF_ECUDA, "sweep launch failed");
   ++c->launches;
   return NEGF_OK;
@@ -629,7 +643,10 @@ static int mixed_recompute(Ctx* c, Plan& P) {
     const int cls = group_class(g);
     const int n = (int)redo[g].size();
     const int grid = std::max(1, std::min(P.grid[g + 5], cls < 2 ? (n + 7) / 8 : n));
-    int rc = launch_group(c, P, g, (const int*)B.order2.p + off[g], n, grid, nullptr, nullptr);
+    // the flagged energies are usually a fraction of a wave: spread them over wider CTAs
+    // when that still holds them all at once (else the FP64 group's own width)
+    const int w = (cls == 2 && c->opts.blk_warps == 0) ? partial_wave_width(c, false, P.gb[g], P.gm[g], n) : 0;
+    int rc = launch_group(c, P, g, (const int*)B.order2.p + off[g], n, grid, nullptr, nullptr, w);
     if (rc) return rc;
   }
   return NEGF_OK;
