@@ -1,7 +1,7 @@
 """Mixed-precision path: complex64 sweep of the real-axis lanes, FP64 contour lanes, FP64
 recompute of flagged energies (sum-rule residual above the threshold, or a lead subband
 edge within the window).  Errors are measured against the FP64 oracle per output; the
-bounds stated here are the ones the design doc quotes."""
+bounds stated here are the documented bounds of the path."""
 import numpy as np
 import pytest
 
