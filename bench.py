@@ -126,6 +126,30 @@ class Clocks:
                     reasons=sorted(reasons), samples=len(sm))
 
 
+def rank_gate_voltage(rank):
+    """Each rank solves its own bias point: V_GS = 0.2 V + 0.05 V per rank (weak scaling,
+    no collective on the data path)."""
+    return 0.2 + 0.05 * rank
+
+
+def max_over_ranks(ms, world):
+    """The slowest rank's step time (the job's step time); one all-reduce on the host side
+    of the timing, never inside the timed region."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step, world, t_max_ms):
+    """Whole-job throughput: the units of every rank over the slowest rank's step time."""
+    return world * units_per_step / (t_max_ms * 1e-3)
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -209,7 +233,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     ctx = negf.Context(device=local, stream=stream.cuda_stream)
-    V_GS = 0.2 + 0.05 * rank
+    V_GS = rank_gate_voltage(rank)
     dev, w = build_workload(ctx, negf, synth, V_GS)
     N, n_real, n_cont = w["N"], w["n_real"], w["n_cont"]
     units_per_step = N * (n_real + n_cont)
@@ -243,12 +267,8 @@ def run_ours(args):
     clocks = clk.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
     ctx.sc_end(dev)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * units_per_step / (t_max * 1e-3)
+    t_max = max_over_ranks(ms, world)
+    value = job_value(units_per_step, world, t_max)
 
     # ---- dominant kernel: the block sweep, timed with events on the launching stream
     ctx.profile(True)
