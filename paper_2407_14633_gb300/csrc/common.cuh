@@ -236,6 +236,7 @@ struct ScDev {
 };
 int launch_broyden(const ScDev* devs, int n, cudaStream_t s);
 int launch_poisson(const ScDev* devs, int n, cudaStream_t s);
+int launch_gather_states(const ScDev* devs, int n, int* out, cudaStream_t s);
 
 // host quadrature helper: the upper semicircle contour over [E_B, E_end]
 void contour_arc(double E_B, double E_end, int n, double* z, double* zw);

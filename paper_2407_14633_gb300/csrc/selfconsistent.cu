@@ -145,4 +145,14 @@ int launch_poisson(const ScDev* devs, int n, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// state flag of every solve in one array (one host read per serving step)
+__global__ void gather_states_kernel(const ScDev* devs, int n, int* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = *devs[i].state;
+}
+int launch_gather_states(const ScDev* devs, int n, int* out, cudaStream_t s) {
+  if (n <= 0) return 0;
+  gather_states_kernel<<<(n + 255) / 256, 256, 0, s>>>(devs, n, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 }  // namespace negf

@@ -5,7 +5,8 @@
 // while their estimated device memory fits the budget, then advances every active request
 // by one self-consistent iteration: one Poisson launch (a CTA per request), one batched
 // NEGF sweep over all active devices (one work-item list, longest lanes first), one
-// second-stage reduction and one Broyden launch (a CTA per request).  Requests that enter
+// second-stage reduction and one Broyden launch (a CTA per request).  While the set of
+// active requests is unchanged the step is replayed from a captured CUDA graph.  Requests that enter
 // while others run join the next step, so their work overlaps on the GPU.  Each request's
 // arithmetic -- its lanes, its partial sums, its reductions -- is the same alone and in any
 // mix, so its result is bitwise the same.
@@ -64,7 +65,19 @@ struct Serve {
   Plan plan;
   bool plan_valid = false;
   DBuf sc_desc;
+  DBuf states_d;                 // gathered state flags of the active solves
+  int* states_h = nullptr;       // pinned host copy
+  int states_cap = 0;
+  // one scheduler step captured as a CUDA graph, replayed while the membership is unchanged
+  cudaGraphExec_t graph = nullptr;
+  uint64_t graph_kernels = 0;
+  void drop_graph() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+  }
   ~Serve() {
+    drop_graph();
+    if (states_h) cudaFreeHost(states_h);
     for (auto& kv : all) delete kv.second;
   }
 };
@@ -76,8 +89,10 @@ void serve_free(Ctx* c) {
     for (DBuf* b : {&r->nin, &r->nold, &r->fold, &r->V, &r->W, &r->n0, &r->hist, &r->m, &r->state_d, &r->cp})
       c->arena.release(*b);
   }
+  s->drop_graph();
   free_plan_bufs(c, s->bufs);
   c->arena.release(s->sc_desc);
+  c->arena.release(s->states_d);
   delete s;
   c->serve = nullptr;
 }
@@ -239,6 +254,7 @@ int step_locked(Ctx* c, Serve* s, int* n_active) {
       // the batch plan is rebuilt after admission anyway; its staging is released first so
       // the set-up of the new request (its neutral charge) has room for its own sweep
       cudaStreamSynchronize(c->stream);
+      s->drop_graph();
       free_plan_bufs(c, s->bufs);
       s->plan_valid = false;
       released = true;
@@ -270,28 +286,68 @@ int step_locked(Ctx* c, Serve* s, int* n_active) {
   // plan over all active devices (rebuilt when membership changes)
   const int na = (int)s->active.size();
   if (changed || !s->plan_valid) {
+    s->drop_graph();
     std::vector<Dev*> devs;
     for (Req* r : s->active) devs.push_back(find_device(c, r->dev));
     int rc = build_plan(c, devs, nullptr, -1, s->plan, &s->bufs);
     if (rc) return rc;
     std::vector<ScDev> sds;
     for (Req* r : s->active) sds.push_back(r->sd);
-    if (!ensure(c, s->sc_desc, sizeof(ScDev) * na)) return NEGF_ENOMEM;
+    if (!ensure(c, s->sc_desc, sizeof(ScDev) * na) || !ensure(c, s->states_d, sizeof(int) * na)) return NEGF_ENOMEM;
     if (cudaMemcpy(s->sc_desc.p, sds.data(), sizeof(ScDev) * na, cudaMemcpyHostToDevice) != cudaSuccess)
       return set_err(c, NEGF_ECUDA, "upload failed");
+    if (na > s->states_cap) {
+      if (s->states_h) cudaFreeHost(s->states_h);
+      s->states_h = nullptr;
+      s->states_cap = 0;
+      if (cudaMallocHost(&s->states_h, sizeof(int) * na) != cudaSuccess) return set_err(c, NEGF_ENOMEM, "pinned buffer");
+      s->states_cap = na;
+    }
     s->plan_valid = true;
   }
   const ScDev* dsc = (const ScDev*)s->sc_desc.p;
-  if (launch_poisson(dsc, na, c->stream)) return set_err(c, NEGF_ECUDA, "poisson launch failed");
-  int rc = launch_plan(c, s->plan);
-  if (rc) return rc;
-  if (launch_broyden(dsc, na, c->stream)) return set_err(c, NEGF_ECUDA, "broyden launch failed");
-  c->launches += 2;
-  std::vector<int> st(na);
-  for (int i = 0; i < na; ++i)
-    if (cudaMemcpyAsync(&st[i], s->active[i]->state_d.p, 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
-      return set_err(c, NEGF_ECUDA, "state read failed");
-  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return set_err(c, NEGF_ECUDA, "serving step failed");
+  int* states = (int*)s->states_d.p;
+  // Poisson -> batched sweep -> reduce -> Broyden -> gathered state flags.  The mixed
+  // precision path decides its recompute on the host, so it is launched directly; otherwise
+  // the step is captured once per membership and replayed.
+  auto enqueue = [&]() -> int {
+    if (launch_poisson(dsc, na, c->stream)) return set_err(c, NEGF_ECUDA, "poisson launch failed");
+    int rc = launch_plan(c, s->plan);
+    if (rc) return rc;
+    if (launch_broyden(dsc, na, c->stream) || launch_gather_states(dsc, na, states, c->stream))
+      return set_err(c, NEGF_ECUDA, "broyden launch failed");
+    c->launches += 3;
+    return NEGF_OK;
+  };
+  const bool graphable = s->plan.prec != NEGF_PREC_MIXED && !c->profile;
+  if (graphable && !s->graph) {
+    const uint64_t l0 = c->launches;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const int rc = enqueue();
+      const cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ec == cudaSuccess && g && cudaGraphInstantiate(&s->graph, g, 0) != cudaSuccess) s->graph = nullptr;
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    s->graph_kernels = c->launches - l0;
+    c->launches = l0;
+  }
+  if (s->graph) {
+    if (cudaGraphLaunch(s->graph, c->stream) != cudaSuccess) return set_err(c, NEGF_ECUDA, "graph launch failed");
+    c->launches += s->graph_kernels;
+  } else {
+    const int rc = enqueue();
+    if (rc) return rc;
+  }
+  if (cudaMemcpyAsync(s->states_h, states, sizeof(int) * na, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return set_err(c, NEGF_ECUDA, "serving step failed");
+  std::vector<int> st(s->states_h, s->states_h + na);
   std::vector<Req*> keep;
   for (int i = 0; i < na; ++i) {
     Req* r = s->active[i];
