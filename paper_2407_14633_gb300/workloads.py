@@ -28,6 +28,32 @@ def build_uneven(ctx, w, n_devices=None):
     return devs
 
 
+def modespace_small(reps=20):
+    """The small plain-FP64 case: (17,0) mode space, N = 64, 256 midpoint + 64 contour
+    energies, modes j = 1 (literal) and j = 6; one negf_compute per call (latency-bound)."""
+    out = {}
+    for j in (1, 6):
+        w = synth.modespace_small(j)
+        with negf.Context() as ctx:
+            dev = ctx.device_create(w["N"], block=1, rings_per_block=1, n_chains=1)
+            ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], [j], w["U_S"], w["U_D"])
+            ctx.set_potential(dev, w["U"])
+            ctx.set_grid_spec(dev, w["mu_S"], w["mu_D"], w["kT"], w["eta"], w["E_B"], w["n_real"], w["n_cont"],
+                              rule=negf.RULE_MIDPOINT, E_min=-1.0, E_max=1.0)
+            ctx.compute([dev])
+            ctx.profile(True)
+            ctx.kernel_time()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                ctx.compute([dev])
+            wall = (time.perf_counter() - t0) / reps
+            ms, k = ctx.kernel_time()
+        units = w["N"] * (w["n_real"] + w["n_cont"])
+        out["j=%d" % j] = {"sweep_ms": ms / max(k, 1), "updates_per_s_sweep": units / (ms / max(k, 1) * 1e-3),
+                           "call_ms": wall * 1e3, "updates_per_s_call": units / wall}
+    return out
+
+
 def batched_uneven(reps=3):
     """All 64 uneven devices in one negf_compute (one launch per kernel class and element
     type), complex128 and complex64; updates counted per (ring, energy, mode)."""
