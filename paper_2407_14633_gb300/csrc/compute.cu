@@ -20,11 +20,8 @@ namespace {
 
 int kernel_class(const Dev* d) { return d->block == 1 ? 0 : (d->block == 2 ? 1 : 2); }
 
-struct Tune {
-  int block_threads = 256;  // thread-per-lane kernels
-  int blk_warps = 1;        // warps per CTA of the warp-per-lane kernel
-};
-
+// threads per CTA of the thread-per-lane (1 x 1, 2 x 2) sweeps: eight warps, one item each
+constexpr int CHAIN_BLOCK_THREADS = 256;
 
 }  // namespace
 
@@ -398,9 +395,8 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
   }
 
   // launch geometry and staging per group (staging sized for FP64 elements)
-  const Tune tune;
-  P.block_threads = tune.block_threads;
-  const size_t csmem = (size_t)(tune.block_threads / 32) * 32 * 33 * sizeof(double);
+  P.block_threads = CHAIN_BLOCK_THREADS;
+  const size_t csmem = (size_t)(CHAIN_BLOCK_THREADS / 32) * 32 * 33 * sizeof(double);
   long long stage_bytes = 0;
   for (int g = 0; g < NGROUPS; ++g) {
     const int cls = group_class(g);
@@ -413,8 +409,8 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     const bool f32 = group_f32(g);
     int per_sm, wpb;
     if (cls < 2) {
-      per_sm = sweep_chain_occupancy_t(f32, cls, tune.block_threads, csmem);
-      wpb = tune.block_threads / 32;
+      per_sm = sweep_chain_occupancy_t(f32, cls, CHAIN_BLOCK_THREADS, csmem);
+      wpb = CHAIN_BLOCK_THREADS / 32;
     } else {
       const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16, P.gw[g]);
       if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
@@ -438,14 +434,14 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     for (int g = 0; g < 5; ++g) {
       if (!P.ncls[g + 5]) continue;
       const int cls = group_class(g);
-      const int wpb = cls < 2 ? tune.block_threads / 32 : 1;
+      const int wpb = cls < 2 ? CHAIN_BLOCK_THREADS / 32 : 1;
       stage_bytes = std::max(stage_bytes, P.stride[g] * (long long)P.grid[g + 5] * wpb);
       if (cls == 2) {
         const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], 16, P.gw[g]);
         if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
         sweep_blk_occupancy_t(false, P.gw[g], P.gb[g], P.gm[g]);
       } else {
-        sweep_chain_occupancy_t(false, cls, tune.block_threads, csmem);
+        sweep_chain_occupancy_t(false, cls, CHAIN_BLOCK_THREADS, csmem);
       }
     }
 
@@ -486,7 +482,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       stage_bytes = 0;
       for (int g = 0; g < NGROUPS; ++g) {
         if (!P.ncls[g]) continue;
-        const int wpb = group_class(g) < 2 ? tune.block_threads / 32 : 1;
+        const int wpb = group_class(g) < 2 ? CHAIN_BLOCK_THREADS / 32 : 1;
         // an FP32 group's grid also runs its FP64 recompute, with the FP64 stride
         const long long per = std::max(P.stride[g], P.stride[g % 5]) * wpb;
         const long long fit = per > 0 ? cap / per : 1;
