@@ -18,6 +18,8 @@ Current (reading: the Landauer form of Eq. deviceCharacteristics, which the lite
 Tr[F Gamma A + i Gamma G^<] equals as eta -> 0 without the spurious 2 eta Gamma G G^dagger f
 term):  I = g_s (e^2/h) sum_k w_k T(E_k) [f_S(E_k) - f_D(E_k)]  in ampere, energies in eV.
 
+Zero-bias conductance (Eq. zeroBiasG): G = g_s (e^2/h) sum_k w_k T(E_k) (-df/dE)(E_k - mu).
+
 Parity: pinned (neutrality n0 = g_s g_b / 2 per site, zero bias => I = 0, contour ==
 real-axis integral at equilibrium, real space == sum of modes).
 """
@@ -103,3 +105,25 @@ def neutral_charge(device, n_cont, E_B, method="analytic", chunk=64):
         chains.append(Chain(ch.Hdiag, ch.Hup, ch.site_ring, lS, lD, ch.g_b))
     r = negf_evaluate(Device(device.n_rings, chains), zero, grid, method, chunk)
     return r["n_cont"]
+
+
+def minus_dfermi(x, kT):
+    """-df/dE of the Fermi function at x = E - mu: (1/kT) f (1 - f) = 1 / (4 kT cosh^2(x / 2kT))."""
+    x = np.asarray(x, dtype=np.float64)
+    return 1.0 / (4.0 * kT * np.cosh(x / (2.0 * kT)) ** 2)
+
+
+def zero_bias_conductance(T, E, w, mu, kT):
+    """Zero-bias conductance (Eq. zeroBiasG, Sec. 2.2.1): G = G_0 integral T(E) (-df/dE) dE with
+    G_0 = g_s e^2/h, discretised on the real-axis rule (E_k, w_k) that T was evaluated on:
+
+      G = g_s (e^2/h) sum_k w_k T(E_k) (-df/dE)(E_k - mu)     [siemens]
+
+    T is the transmission per energy summed over chains with their band degeneracy (the
+    quantity ``negf_evaluate`` reports), so one open spin-degenerate mode-space subband
+    (g_b = 2) inside a band contributes 2 G_0 = 4 e^2/h.
+
+    Parity: pinned (closed forms for constant and exponential T, ballistic plateau).
+    """
+    T = np.asarray(T, dtype=np.float64)
+    return G_SPIN * E2_OVER_H * float(np.sum(np.asarray(w) * T * minus_dfermi(np.asarray(E) - mu, kT)))

@@ -101,3 +101,42 @@ def test_current_sign_and_units():
     expect = 2.0 * 2.0 * chg.E2_OVER_H * (mu_S - mu_D)
     assert abs(r["I"] - expect) < 1e-6 * expect
     assert abs(chg.E2_OVER_H - 3.874045865e-5) < 1e-13
+
+
+# ---- zero-bias conductance (Eq. zeroBiasG)
+
+def test_conductance_of_constant_transmission_is_fermi_difference():
+    # integral_a^b (-df/dE) dE = f(a - mu) - f(b - mu): with T == 3 on a Gauss-Legendre rule over
+    # mu -+ 14 kT, G = 3 g_s (e^2/h) (f(-14 kT) - f(14 kT)) = 3 g_s (e^2/h) tanh(7)
+    mu, kT = 0.13, 0.025
+    E, w = q.real_axis_gauss(mu - 14 * kT, mu + 14 * kT, 200)
+    G = chg.zero_bias_conductance(np.full(E.size, 3.0), E, w, mu, kT)
+    expect = 3.0 * 2.0 * chg.E2_OVER_H * (1.0 / (1.0 + np.exp(-14.0)) - 1.0 / (1.0 + np.exp(14.0)))
+    assert abs(G - expect) < 1e-13 * expect
+    assert abs(expect / (6.0 * chg.E2_OVER_H) - np.tanh(7.0)) < 1e-15
+
+
+@pytest.mark.parametrize("a", [-8.0, 3.0, 8.0])
+def test_conductance_of_exponential_transmission_closed_form(a):
+    # integral e^{a x} (-df/dx) dx over the real line = pi a kT / sin(pi a kT) (|a kT| < 1); the
+    # window mu -+ 40 kT leaves tails below 1e-13 for |a kT| <= 0.2
+    mu, kT = -0.07, 0.025
+    E, w = q.real_axis_gauss(mu - 40 * kT, mu + 40 * kT, 400)
+    G = chg.zero_bias_conductance(np.exp(a * (E - mu)), E, w, mu, kT)
+    x = np.pi * a * kT
+    assert abs(G / (2.0 * chg.E2_OVER_H) - x / np.sin(x)) < 1e-12
+
+
+def test_conductance_ballistic_plateau_is_two_quanta_per_subband():
+    # flat (17,0) mode-space wire, mode j = 6, mu inside its first subband (edge 0.293 eV):
+    # one open spin-degenerate channel of band degeneracy 2, G = 2 G_0 = 4 e^2/h up to the
+    # Fermi tails outside the window, and T(E) = 2 at every node
+    N = 6
+    dev = mdl.cnt_build("mode", 17, T_HOP, N, 0.0, 0.0, modes=(6,))
+    mu, kT = 0.9, 0.005
+    g = q.bias_grid(mu, mu, kT, 96, 4, E_B=-10.0, eta=1e-9)
+    r = chg.negf_evaluate(dev, np.zeros(N), g)
+    assert np.max(np.abs(r["T"] - 2.0)) < 1e-8
+    G = chg.zero_bias_conductance(r["T"], g["E"], g["w"], mu, kT)
+    expect = 2.0 * 2.0 * chg.E2_OVER_H * np.tanh(7.0)
+    assert abs(G - expect) < 1e-8 * expect

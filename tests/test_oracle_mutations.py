@@ -140,3 +140,31 @@ def test_half_filling_pin_rejects(name, old, new):
         pytest.fail("mutation site %r not found once in oracle/charge.py" % old)
     m = mutant("charge", old, new)
     assert half_filling_gap(m) > 0.1, name
+
+
+def conductance_gap(charge_mod):
+    """Largest relative miss of the two closed forms of the conductance pins."""
+    zbc = charge_mod["zero_bias_conductance"] if isinstance(charge_mod, dict) else charge_mod.zero_bias_conductance
+    e2h = 1.602176634e-19 ** 2 / 6.62607015e-34
+    mu, kT = 0.13, 0.025
+    E, w = qd.real_axis_gauss(mu - 40 * kT, mu + 40 * kT, 400)
+    const = zbc(np.ones(E.size), E, w, mu, kT) / (2.0 * e2h)
+    fdiff = 1.0 / (1.0 + np.exp(-40.0)) - 1.0 / (1.0 + np.exp(40.0))
+    x = np.pi * 5.0 * kT
+    expo = zbc(np.exp(5.0 * (E - mu)), E, w, mu, kT) / (2.0 * e2h)
+    return max(abs(const - fdiff), abs(expo - x / np.sin(x)))
+
+
+def test_real_conductance_passes_its_pins():
+    from oracle import charge as ch
+    assert conductance_gap(ch) < 1e-12
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("cosh argument without the factor 1/2", "np.cosh(x / (2.0 * kT))", "np.cosh(x / kT)"),
+    ("f (1 - f) without 1/kT", "1.0 / (4.0 * kT * np.cosh", "1.0 / (4.0 * np.cosh"),
+    ("weights dropped", "np.sum(np.asarray(w) * T *", "np.sum(T *"),
+])
+def test_conductance_pin_rejects(name, old, new):
+    m = mutant("charge", old, new)
+    assert conductance_gap(m) > 1e-3, name
