@@ -127,3 +127,33 @@ def zero_bias_conductance(T, E, w, mu, kT):
     """
     T = np.asarray(T, dtype=np.float64)
     return G_SPIN * E2_OVER_H * float(np.sum(np.asarray(w) * T * minus_dfermi(np.asarray(E) - mu, kT)))
+
+
+def ring_integrand(device, U, grid, ring, method="analytic", chunk=64):
+    """Charge integrand of one ring on the real axis (Sec. 3.3, the A_1 F_1 + A_2 F_2 curve the
+    paper plots at the centre of the channel), per unit energy:
+
+      I_r(E_k) = sum_chains (g_s g_b / 2 pi) [f_S(E_k) Tr_r A_S(E_k) + f_D(E_k) Tr_r A_D(E_k)],
+
+    so that sum_k w_k I_r(E_k) is the real-axis part of n_r.  Parity: pinned (the
+    closed-form local density of states of the infinite dimerised chain; sum rule against
+    ``negf_evaluate``).
+    """
+    E, fS, fD, eta = grid["E"], grid["fS"], grid["fD"], grid["eta"]
+    out = np.zeros(E.size)
+    for ch in device.chains:
+        g = G_SPIN * ch.g_b
+        for k0 in range(0, E.size, chunk):
+            sl = slice(k0, min(E.size, k0 + chunk))
+            r = rgf_lanes(ch, U, E[sl] + 1j * eta, method, spectral=True)
+            aS = ring_sum(ch, device.n_rings, r["AS"])[:, ring]
+            aD = ring_sum(ch, device.n_rings, r["AD"])[:, ring]
+            out[sl] += g / (2 * np.pi) * (fS[sl] * aS + fD[sl] * aD)
+    return out
+
+
+def singularity_peak(E, integrand):
+    """Location E_s of the integrand's peak (Sec. 3.3): the node of largest value, the first
+    such node when several are equal.  Returns (E_s, index)."""
+    k = int(np.argmax(np.asarray(integrand)))
+    return float(E[k]), k

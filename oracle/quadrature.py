@@ -155,3 +155,53 @@ def neutral_grid(n_cont, E_B):
     return dict(E=np.zeros(0), w=np.zeros(0), fS=np.zeros(0), fD=np.zeros(0), eta=0.0,
                 z=z, c=zw.astype(complex), E_min=0.0, E_max=0.0, mu_min=0.0, kT=0.0,
                 mu_S=0.0, mu_D=0.0)
+
+
+def segment_points(a, b, density, kT):
+    """Number of Gauss-Legendre points of one sub-interval [a, b] at `density` points per kT
+    (Sec. 3.3): ceil(density * ((b - a) / kT) - 1e-6), at least one, none for an empty
+    interval (reading: the slack of a millionth of a point keeps a width that is a whole
+    number of kT, up to rounding, from gaining a point)."""
+    if not b > a:
+        return 0
+    return max(1, int(np.ceil(density * ((b - a) / kT) - 1e-6)))
+
+
+def semi_adaptive_rule(E_min, E_max, E_l1, E_l2, densities, kT):
+    """Real-axis rule of the semi-adaptive scheme (Sec. 3.3): the path E_min -> E_max split
+    at E_l1 <= E_l2 into three sub-intervals, each integrated with its own Gauss-Legendre
+    rule whose point count follows the user's density (points per kT) of that sub-interval.
+
+    Readings: E_l1 and E_l2 are clipped into [E_min, E_max] (E_l2 no lower than E_l1); a
+    sub-interval of zero width gets no points.  Returns (E, w, (n1, n2, n3)).
+    """
+    l1 = min(max(E_l1, E_min), E_max)
+    l2 = min(max(E_l2, l1), E_max)
+    Es, ws, ns = [], [], []
+    for (a, b), d in zip(((E_min, l1), (l1, l2), (l2, E_max)), densities):
+        n = segment_points(a, b, d, kT)
+        ns.append(n)
+        if n:
+            e, w = real_axis_gauss(a, b, n)
+            Es.append(e)
+            ws.append(w)
+    return np.concatenate(Es), np.concatenate(ws), tuple(ns)
+
+
+def refined_limits(E_s, a, b, kT):
+    """Limits after locating the singularity peak E_s (Sec. 3.3): E_l1 = E_s - a kT,
+    E_l2 = E_s + b kT (reading: the printed "E_l1 = E_l1 - a kT" takes E_s as its base, as
+    E_l2 does; a = 3, b = 1 are the paper's typical values)."""
+    return E_s - a * kT, E_s + b * kT
+
+
+def adaptive_grid(mu_S, mu_D, kT, E_l1, E_l2, densities, n_cont, E_B, eta, E_min=None, E_max=None,
+                  f1=F1_DEFAULT, f2=F2_DEFAULT):
+    """``bias_grid`` with the semi-adaptive real-axis rule in place of the single rule; the
+    contour part is unchanged.  Also returns the clipped limits and segment sizes."""
+    g = bias_grid(mu_S, mu_D, kT, 1, n_cont, E_B, eta, E_min=E_min, E_max=E_max, f1=f1, f2=f2)
+    E, w, ns = semi_adaptive_rule(g["E_min"], g["E_max"], E_l1, E_l2, densities, kT)
+    l1 = min(max(E_l1, g["E_min"]), g["E_max"])
+    g.update(E=E, w=w, fS=fermi(E - mu_S, kT), fD=fermi(E - mu_D, kT), E_l1=l1,
+             E_l2=min(max(E_l2, l1), g["E_max"]), segments=ns, densities=tuple(densities))
+    return g

@@ -27,8 +27,15 @@ the coaxial gate capacitance per length C_g = 2 pi eps0 eps_r / ln((2 t_ox + d)/
 dx = 3 a_cc / 4 = 0.1065 nm (512 rings span 54.53 nm in Table 1), eps_r = 3.9, d = 1.3 nm
 (Sec. 3.1), t_ox = 10 nm (Sec. 3.4).  Solved with the Thomas algorithm.
 
+Semi-adaptive real-axis grid inside the loop (Sec. 3.3): the limits E_l1, E_l2 are set from
+the singularity peak of the centre-ring integrand at the first iteration of a solve and again
+every `period` iterations (the paper uses 50); at such an iteration the peak is located with
+the iteration's own potential on the grid in use, then the grid is rebuilt before the NEGF
+evaluation.
+
 Parity: pinned (Thomas vs dense solve, closed-form solution for n = n0, Broyden vs the
-dense rank-one form, convergence on a linear map).
+dense rank-one form, convergence on a linear map; the refining loop with a period beyond its
+iteration count against the plain loop on the refined grid).
 """
 from dataclasses import dataclass
 import numpy as np
@@ -196,3 +203,39 @@ def sc_solve(evaluate, U0, n0, p, zeta=0.1, M=64, tol=1e-8):
         br.step(r["n"])
     return dict(converged=False, iterations=M, history=history, n=r["n"],
                 n_in=br.n_in.copy(), U=U, T=r["T"], I=r["I"])
+
+
+def sc_solve_adaptive(evaluate, integrand, make_grid, U0, n0, p, limits, a, b, kT, period,
+                      zeta=0.1, M=64, tol=1e-8):
+    """``sc_solve`` with the semi-adaptive real-axis grid (Sec. 3.3).
+
+    evaluate(U, grid) -> NEGF dict; integrand(U, grid) -> the refinement ring's integrand at
+    the grid's real-axis nodes; make_grid(E_l1, E_l2) -> grid.  limits: the initial (E_l1,
+    E_l2).  At iteration 0 and at every iteration that is a multiple of `period` (period 0:
+    the first only): E_s = peak of integrand(U, grid), limits = (E_s - a kT, E_s + b kT),
+    grid = make_grid(limits).  Returns the ``sc_solve`` dict plus grid, limits and the list
+    of located peaks.
+    """
+    from .quadrature import refined_limits
+    from .charge import singularity_peak
+    grid = make_grid(*limits)
+    br = Broyden(poisson_charge(U0, n0, p), zeta, M)
+    history, peaks = [], []
+    r = None
+    U = None
+    for it in range(M):
+        U = poisson_solve(br.n_in, n0, p)
+        if it == 0 or (period > 0 and it % period == 0):
+            E_s, _ = singularity_peak(grid["E"], integrand(U, grid))
+            peaks.append(E_s)
+            limits = refined_limits(E_s, a, b, kT)
+            grid = make_grid(*limits)
+        r = evaluate(U, grid)
+        eps = residual(br.n_in, r["n"])
+        history.append(eps)
+        if eps < tol:
+            return dict(converged=True, iterations=it + 1, history=history, n=r["n"], n_in=br.n_in.copy(),
+                        U=U, T=r["T"], I=r["I"], grid=grid, limits=limits, peaks=peaks)
+        br.step(r["n"])
+    return dict(converged=False, iterations=M, history=history, n=r["n"], n_in=br.n_in.copy(), U=U,
+                T=r["T"], I=r["I"], grid=grid, limits=limits, peaks=peaks)

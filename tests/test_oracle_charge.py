@@ -140,3 +140,54 @@ def test_conductance_ballistic_plateau_is_two_quanta_per_subband():
     G = chg.zero_bias_conductance(r["T"], g["E"], g["w"], mu, kT)
     expect = 2.0 * 2.0 * chg.E2_OVER_H * np.tanh(7.0)
     assert abs(G - expect) < 1e-8 * expect
+
+
+# ---- charge integrand of one ring and its peak (semi-adaptive grid, Sec. 3.3)
+
+def dimer_ldos(E, t1, t2):
+    """Local density of states per site of the infinite chain with alternating bonds t1, t2:
+    |E| / (pi sqrt(((t1+t2)^2 - E^2)(E^2 - (t1-t2)^2))) inside the bands, 0 in the gaps."""
+    p = ((t1 + t2) ** 2 - E ** 2) * (E ** 2 - (t1 - t2) ** 2)
+    out = np.zeros_like(E)
+    ok = p > 0
+    out[ok] = np.abs(E[ok]) / (np.pi * np.sqrt(p[ok]))
+    return out
+
+
+def test_ring_integrand_is_the_infinite_chain_ldos():
+    # flat mode-space wire identical to its leads = the infinite dimerised chain: at every ring
+    # A_S + A_D = 2 pi rho(E) (eta -> 0), so with f = 1 the integrand is g_s g_b rho(E)
+    N = 8
+    t1, t2 = abs(T_HOP), abs(2 * T_HOP * np.cos(6 * np.pi / 17))
+    dev = mdl.cnt_build("mode", 17, T_HOP, N, 0.0, 0.0, modes=(6,))
+    E = np.concatenate([np.linspace(-1.0, -0.4, 7), np.linspace(0.4, 1.0, 7), [0.1, -0.2]])
+    g = dict(E=E, w=np.ones(E.size), fS=np.ones(E.size), fD=np.ones(E.size), eta=1e-9,
+             z=np.zeros(0, complex), c=np.zeros(0, complex))
+    for ring in (0, N // 2, N - 1):
+        I = chg.ring_integrand(dev, np.zeros(N), g, ring)
+        want = 2.0 * 2.0 * dimer_ldos(E, t1, t2)
+        assert np.max(np.abs(I - want)) < 1e-6 * np.max(want)
+    assert np.all(np.abs(I[-2:]) < 1e-6)   # gap energies
+
+
+def test_singularity_peak_is_first_node_above_band_edge():
+    N = 8
+    t1, t2 = abs(T_HOP), abs(2 * T_HOP * np.cos(6 * np.pi / 17))
+    edge = abs(t1 - t2)
+    dev = mdl.cnt_build("mode", 17, T_HOP, N, 0.0, 0.0, modes=(6,))
+    E, w = q.real_axis_gauss(0.2, 0.6, 120)
+    g = dict(E=E, w=w, fS=q.fermi(E - 5.0, 0.025), fD=q.fermi(E - 5.0, 0.025), eta=1e-9,
+             z=np.zeros(0, complex), c=np.zeros(0, complex))
+    Es, k = chg.singularity_peak(E, chg.ring_integrand(dev, np.zeros(N), g, N // 2))
+    assert k == int(np.argmax(E > edge)) and Es == E[k]
+
+
+def test_ring_integrand_sums_to_real_axis_charge():
+    N = 14
+    dev = mdl.cnt_build("mode", 17, T_HOP, N, 0.0, -0.2, modes=(6, 5))
+    U = np.linspace(0.0, -0.2, N) + 0.1 * np.exp(-((np.arange(N) - 6.5) ** 2) / 6)
+    g = q.bias_grid(0.0, -0.2, 0.025, 64, 8, E_B=-10.0, eta=1e-6)
+    r = chg.negf_evaluate(dev, U, g)
+    for ring in (3, N // 2, N - 2):
+        I = chg.ring_integrand(dev, U, g, ring)
+        assert abs(np.sum(g["w"] * I) - r["n_real"][ring]) < 1e-12 * r["n_real"][ring]

@@ -168,3 +168,69 @@ def test_real_conductance_passes_its_pins():
 def test_conductance_pin_rejects(name, old, new):
     m = mutant("charge", old, new)
     assert conductance_gap(m) > 1e-3, name
+
+
+def adaptive_gap(quad_mod):
+    """Miss of the semi-adaptive rule on a Lorentzian peak and on its segment counts."""
+    rule = quad_mod["semi_adaptive_rule"] if isinstance(quad_mod, dict) else quad_mod.semi_adaptive_rule
+    lim = quad_mod["refined_limits"] if isinstance(quad_mod, dict) else quad_mod.refined_limits
+    kT, Es, gam, a, b = 0.025, -0.45, 1e-3, -0.75, 0.35
+    l1, l2 = lim(Es, 3.0, 1.0, kT)
+    E, w, ns = rule(a, b, l1, l2, (10, 400, 10), kT)
+    exact = np.arctan((b - Es) / gam) - np.arctan((a - Es) / gam)
+    miss = abs(np.sum(w * gam / ((E - Es) ** 2 + gam ** 2)) - exact) / exact
+    return max(miss, 0.0 if ns == (90, 1600, 310) else 1.0)
+
+
+def test_real_adaptive_rule_passes_its_pin():
+    assert adaptive_gap(qd) < 1e-10
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("lower limit moved the wrong way", "return E_s - a * kT, E_s + b * kT", "return E_s + a * kT, E_s + b * kT"),
+    ("densities applied to the wrong segments", "zip(((E_min, l1), (l1, l2), (l2, E_max)), densities)",
+     "zip(((E_min, l1), (l1, l2), (l2, E_max)), (densities[1], densities[0], densities[2]))"),
+])
+def test_adaptive_rule_pin_rejects(name, old, new):
+    m = mutant("quadrature", old, new)
+    assert adaptive_gap(m) > 1e-6, name
+
+
+def peak_gap(charge_mod):
+    """Whether the located peak of the flat wire's integrand is the first node above the edge."""
+    ri = charge_mod["ring_integrand"] if isinstance(charge_mod, dict) else charge_mod.ring_integrand
+    sp = charge_mod["singularity_peak"] if isinstance(charge_mod, dict) else charge_mod.singularity_peak
+    N = 8
+    edge = abs(abs(T_HOP) - abs(2 * T_HOP * np.cos(6 * np.pi / 17)))
+    dev = mdl.cnt_build("mode", 17, T_HOP, N, 0.0, 0.0, modes=(6,))
+    E, w = qd.real_axis_gauss(0.2, 0.6, 120)
+    f = qd.fermi(E - 5.0, 0.025)
+    g = dict(E=E, w=w, fS=f, fD=f, eta=1e-9, z=np.zeros(0, complex), c=np.zeros(0, complex))
+    _, k = sp(E, ri(dev, np.zeros(N), g, N // 2))
+    return 0.0 if k == int(np.argmax(E > edge)) else 1.0
+
+
+def test_real_peak_passes_its_pin():
+    from oracle import charge as ch
+    assert peak_gap(ch) == 0.0
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("smallest value taken for the peak", "k = int(np.argmax(np.asarray(integrand)))",
+     "k = int(np.argmin(np.asarray(integrand)))"),
+    ("integrand without the source term", "(fS[sl] * aS + fD[sl] * aD)", "(fD[sl] * aD)"),
+])
+def test_peak_pin_rejects(name, old, new):
+    m = mutant("charge", old, new)
+    if name.startswith("integrand"):
+        # zero-bias flat wire: A_S = A_D, so dropping one term halves the integrand; the peak
+        # moves nowhere, and the sum rule against the real-axis charge catches it instead
+        N = 14
+        dev = mdl.cnt_build("mode", 17, T_HOP, N, 0.0, -0.2, modes=(6,))
+        U = np.linspace(0.0, -0.2, N)
+        g = qd.bias_grid(0.0, -0.2, 0.025, 48, 8, E_B=-10.0, eta=1e-6)
+        from oracle import charge as ch
+        nr = ch.negf_evaluate(dev, U, g)["n_real"][7]
+        assert abs(np.sum(g["w"] * m["ring_integrand"](dev, U, g, 7)) - nr) > 1e-3 * nr, name
+    else:
+        assert peak_gap(m) > 0.0, name

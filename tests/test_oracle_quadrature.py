@@ -73,3 +73,42 @@ def test_bias_grid_window_and_weights():
     # contour weights include f(z - mu_min), which is ~1 on the arc
     z, zw = q.contour_semicircle(-11.0, g["E_min"], 128)
     assert np.max(np.abs(g["c"] - zw)) < 1e-5 * np.max(np.abs(zw))
+
+
+# ---- semi-adaptive real-axis rule (Sec. 3.3)
+
+def test_semi_adaptive_segment_counts_and_exactness():
+    kT = 0.025
+    E, w, ns = q.semi_adaptive_rule(-0.75, 0.35, -0.5, -0.4, (20, 80, 5), kT)
+    # 10 kT at 20 / kT, 4 kT at 80 / kT, 30 kT at 5 / kT
+    assert ns == (200, 320, 150)
+    assert E.size == 670 and np.all(np.diff(E) > 0)
+    a, b = -0.75, 0.35
+    for k in range(0, 40):
+        exact = (b ** (k + 1) - a ** (k + 1)) / (k + 1)
+        assert abs(np.sum(w * E ** k) - exact) < 1e-13 * max(1.0, abs(exact))
+
+
+def test_semi_adaptive_limits_are_clipped():
+    kT = 0.025
+    _, _, ns = q.semi_adaptive_rule(-0.75, 0.35, -2.0, -0.7, (10, 10, 10), kT)
+    assert ns[0] == 0 and ns[1] == 20 and ns[2] == 420
+    _, _, ns = q.semi_adaptive_rule(-0.75, 0.35, 0.3, 9.0, (10, 10, 10), kT)
+    assert ns[2] == 0 and ns[1] == 20
+    _, _, ns = q.semi_adaptive_rule(-0.75, 0.35, -0.2, -0.4, (10, 10, 10), kT)
+    assert ns[1] == 0 and sum(ns) == 220 + 220
+    assert q.refined_limits(-0.45, 3.0, 1.0, kT) == (-0.45 - 3 * kT, -0.45 + kT)
+
+
+def test_semi_adaptive_rule_resolves_a_sharp_peak():
+    # a Lorentzian of width 1 meV (closed-form integral): dense points around the peak get it
+    # to rounding, one Gauss-Legendre rule with the same point count over the whole window does not
+    kT, Es, gam = 0.025, -0.45, 1e-3
+    a, b = -0.75, 0.35
+    exact = np.arctan((b - Es) / gam) - np.arctan((a - Es) / gam)
+    l1, l2 = q.refined_limits(Es, 3.0, 1.0, kT)
+    E, w, ns = q.semi_adaptive_rule(a, b, l1, l2, (10, 400, 10), kT)
+    f = lambda x: gam / ((x - Es) ** 2 + gam ** 2)
+    assert abs(np.sum(w * f(E)) - exact) < 1e-10 * exact
+    Eu, wu = q.real_axis_gauss(a, b, E.size)
+    assert abs(np.sum(wu * f(Eu)) - exact) > 1e-6 * exact
