@@ -347,7 +347,8 @@ def run_ours(args):
     if args.extras and rank == 0:
         from paper_2407_14633_gb300 import workloads
         runs = {"modespace_small": workloads.modespace_small, "batched_uneven": workloads.batched_uneven,
-                "mixed_precision": workloads.mixed_precision, "serving": workloads.serving_sweep}
+                "mixed_precision": workloads.mixed_precision, "serving": workloads.serving_sweep,
+                "gate_sweep": lambda: {"warm": workloads.gate_sweep(), "cold": workloads.gate_sweep(warm=False)}}
         pick = list(runs) if args.extras == "all" else args.extras.split(",")
         line["extras"] = {k: runs[k]() for k in pick}
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -421,8 +422,9 @@ def main():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--extras", nargs="?", const="all", default=None,
-                    help="also run the small, batched-uneven, mixed-precision and serving workloads "
-                         "(or a comma list of modespace_small, batched_uneven, mixed_precision, serving)")
+                    help="also run the small, batched-uneven, mixed-precision, serving and gate-sweep workloads "
+                         "(or a comma list of modespace_small, batched_uneven, mixed_precision, serving, "
+                         "gate_sweep)")
     ap.add_argument("--profile-small", action="store_true",
                     help="reduced case of the block sweep for ncu captures")
     ap.add_argument("--blk-warps", type=int, default=1,

@@ -240,6 +240,20 @@ int negf_sample_lanes(negf_ctx* ctx, int dev, int k_real, const int* idx_real, d
  * contour over [E_B, 0] with occupation 1 and zero potential in the device and leads. */
 int negf_neutral_charge(negf_ctx* ctx, int dev, int n_cont, double E_B, double* n0);
 
+/* Zero-bias conductance (Eq. zeroBiasG, Sec. 2.2.1) of n_devs devices in their current state:
+ *   G = G_0 integral T(E) (-df/dE) dE  ~=  g_s (e^2/h) sum_k w_k T(E_k) (-df/dE)(E_k - mu),
+ * with G_0 = g_s e^2/h (siemens), f the Fermi function at temperature kT (eV), and T(E) the
+ * transmission (summed over chains with g_b) at the real-axis nodes E_k and weights w_k of
+ * each device's grid.  Only the real-axis lanes are swept (T needs no contour); the sum runs
+ * on the GPU in a fixed order, so a device gives the same bits alone or in a batch.  The grid
+ * should cover mu -+ ~14 kT (e.g. negf_set_grid_spec with mu_S = mu_D = mu).  G: n_devs
+ * doubles (host).  T: NULL, or host room for every device's n_real transmissions,
+ * concatenated in the order of devs.  The device's other outputs are overwritten.  Errors:
+ * NEGF_EINVAL (kT <= 0, non-finite mu, a device without real-axis energies or listed twice),
+ * NEGF_ENOTFOUND, NEGF_EBUSY (a device in a self-consistent session). */
+int negf_conductance(negf_ctx* ctx, const int* devs, int n_devs, double mu, double kT, double* G,
+                     double* T);
+
 /* ---- self-consistent loop (Alg. 3) with the 1D Poisson stand-in ------------------------ */
 
 /* Poisson stand-in, one node per ring:

@@ -449,6 +449,8 @@ int negf_destroy(negf_ctx* c) {
     cudaEventDestroy(pr.second);
   }
   free_plan_bufs(c, c->scratch);
+  c->arena.release(c->lane_stats);
+  c->arena.release(c->cond);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return NEGF_OK;

@@ -205,6 +205,17 @@ struct ReduceDev {
 };
 int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s);
 
+// Zero-bias conductance of one device (Eq. zeroBiasG): G = g_s (e^2/h) sum_k w_k T_k (-df/dE)(E_k - mu).
+struct CondDev {
+  int n_real;
+  const double* E;
+  const double* w;
+  const double* T;   // transmission per energy, summed over chains with g_b
+  double mu, kT;
+  double* G;         // output (device)
+};
+int launch_conductance(const CondDev* devs, int n_devs, cudaStream_t s);
+
 // Per-launch layer diagonals of the 1 x 1 chains: hu[l] = Re H_ll + U_l, hu_f its FP32 copy.
 struct PrepDesc {
   int L;

@@ -929,6 +929,61 @@ int negf_neutral_charge(negf_ctx* c, int dev, int n_cont, double E_B, double* n0
   return rc;
 }
 
+int negf_conductance(negf_ctx* c, const int* devs, int n_devs, double mu, double kT, double* G, double* T) {
+  if (!c) return NEGF_EINVAL;
+  if (!devs || !G || n_devs < 1 || !std::isfinite(mu) || !(kT > 0.0) || !std::isfinite(kT))
+    return set_err(c, NEGF_EINVAL, "bad conductance arguments");
+  std::vector<Dev*> list;
+  for (int i = 0; i < n_devs; ++i) {
+    Dev* d = find_dev(c, devs[i]);
+    if (!d) return set_err(c, NEGF_ENOTFOUND, "unknown device");
+    if (d->sc) return set_err(c, NEGF_EBUSY, "device is in a self-consistent session");
+    for (int j = 0; j < i; ++j)
+      if (devs[j] == devs[i]) return set_err(c, NEGF_EINVAL, "device listed twice");
+    int rc = check_ready(c, d);
+    if (rc) return rc;
+    if (d->n_real < 1) return set_err(c, NEGF_EINVAL, "the conductance needs real-axis energies");
+    list.push_back(d);
+  }
+  cudaSetDevice(c->ordinal);
+  // T(E) needs the real-axis lanes only
+  std::vector<ViewOverride> ov(n_devs);
+  for (auto& o : ov) o.n_cont = 0;
+  int rc = run_batch(c, list, &ov, nullptr, nullptr, nullptr, -1);
+  if (rc) return rc;
+  const size_t desc = (size_t)n_devs * sizeof(CondDev);
+  if (!ensure(c, c->cond, desc + (size_t)n_devs * sizeof(double))) return NEGF_ENOMEM;
+  double* gdev = reinterpret_cast<double*>(static_cast<unsigned char*>(c->cond.p) + desc);
+  std::vector<CondDev> cds(n_devs);
+  for (int i = 0; i < n_devs; ++i) {
+    Dev* d = list[i];
+    cds[i].n_real = d->n_real;
+    cds[i].E = (const double*)d->dE.p;
+    cds[i].w = (const double*)d->dw.p;
+    cds[i].T = (const double*)d->dT.p;
+    cds[i].mu = mu;
+    cds[i].kT = kT;
+    cds[i].G = gdev + i;
+  }
+  if (cudaMemcpyAsync(c->cond.p, cds.data(), desc, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return set_err(c, NEGF_ECUDA, "upload failed");
+  if (launch_conductance((const CondDev*)c->cond.p, n_devs, c->stream))
+    return set_err(c, NEGF_ECUDA, "conductance launch failed");
+  ++c->launches;
+  if (cudaMemcpyAsync(G, gdev, (size_t)n_devs * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return set_err(c, NEGF_ECUDA, "copy out failed");
+  if (T) {
+    size_t off = 0;
+    for (Dev* d : list) {
+      if (cudaMemcpyAsync(T + off, d->dT.p, (size_t)d->n_real * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return set_err(c, NEGF_ECUDA, "copy out failed");
+      off += d->n_real;
+    }
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return set_err(c, NEGF_ECUDA, "conductance failed");
+  return NEGF_OK;
+}
+
 }  // extern "C"
 
 namespace negf {

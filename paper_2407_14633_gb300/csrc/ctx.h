@@ -101,6 +101,7 @@ struct Ctx {
   double prof_ms = 0.0;
   uint64_t prof_count = 0;
   DBuf lane_stats;   // 4 counters of negf_sweep_lanes
+  DBuf cond;         // descriptors and outputs of negf_conductance
   // launch shapes (CTA width, resident CTAs per SM) chosen by the autotuner of the
   // wide-block sweep, keyed by (element type, b, m, items); the latest per (type, b, m)
   std::map<std::tuple<int, int, int, int>, std::pair<int, int>> blk_tuned;

@@ -2,7 +2,8 @@
 // sum the per-item partial ring sums in item order (deterministic, independent of the
 // schedule and of the rest of the batch), sum T(E) over chains with their band
 // degeneracy, and reduce the Landauer current I = g_s (e^2/h) sum_k w_k T_k (fS_k - fD_k)
-// with a fixed-shape tree in shared memory.  Also the per-launch layer diagonals of the 1 x 1
+// with a fixed-shape tree in shared memory; the zero-bias conductance (Eq. zeroBiasG) the
+// same way.  Also the per-launch layer diagonals of the 1 x 1
 // chains (prep_kernel), which the sweep would otherwise form in every lane.
 #include <algorithm>
 
@@ -50,6 +51,34 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReduceDev* devs) {
 
 int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s) {
   reduce_kernel<<<n_devs, 256, 0, s>>>(devs);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Zero-bias conductance (Eq. zeroBiasG) from the transmission of the real-axis lanes:
+// G = g_s (e^2/h) sum_k w_k T_k (-df/dE)(E_k - mu), with -df/dE = e / (kT (1 + e)^2),
+// e = exp(-|E - mu| / kT) (no overflow in the tails).  One CTA per device, strided partial
+// sums then a fixed-shape shared-memory tree: the same bits alone or in a batch.
+__global__ void __launch_bounds__(256) conductance_kernel(const CondDev* devs) {
+  const CondDev& D = devs[blockIdx.x];
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < D.n_real; k += blockDim.x) {
+    const double e = exp(-fabs(D.E[k] - D.mu) / D.kT);
+    const double mdf = e / (D.kT * (1.0 + e) * (1.0 + e));
+    acc += D.w[k] * D.T[k] * mdf;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *D.G = 2.0 * kE2H * sh[0];
+}
+
+int launch_conductance(const CondDev* devs, int n_devs, cudaStream_t s) {
+  if (n_devs <= 0) return 0;
+  conductance_kernel<<<n_devs, 256, 0, s>>>(devs);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -96,6 +96,7 @@ _PROTOS = {
     "negf_compute": (C.c_int, [C.c_void_p, _ip, C.c_int, C.POINTER(Out)]),
     "negf_sample_lanes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip, _dp, _dp, C.c_int, _ip, _dp]),
     "negf_neutral_charge": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, _dp]),
+    "negf_conductance": (C.c_int, [C.c_void_p, _ip, C.c_int, C.c_double, C.c_double, _dp, _dp]),
     "negf_poisson_kappa": (C.c_double, [C.c_double, C.c_double, C.c_double, C.c_double]),
     "negf_sc_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Bias), C.POINTER(Poisson), C.POINTER(Broyden),
                                 _dp, C.POINTER(ScResult)]),
@@ -357,6 +358,18 @@ class Context:
         n0 = np.zeros(self._dev[dev]["n_rings"])
         self._chk(self.lib.negf_neutral_charge(self.h, dev, n_cont, E_B, _p(n0)))
         return n0
+
+    def conductance(self, devs, mu, kT, want_T=False):
+        """negf_conductance: zero-bias conductance (S) per device, and optionally T(E) per device."""
+        devs = list(devs)
+        ids = np.ascontiguousarray(devs, dtype=np.int32)
+        G = np.zeros(len(devs))
+        nrs = [self._dev[d].get("n_real", 0) for d in devs]
+        T = np.zeros(max(sum(nrs), 1)) if want_T else None
+        self._chk(self.lib.negf_conductance(self.h, _pi(ids), len(devs), mu, kT, _p(G), _p(T)))
+        if not want_T:
+            return G
+        return G, np.split(T[:sum(nrs)], np.cumsum(nrs)[:-1])
 
     def sc_solve(self, dev, V_DS, V_GS, U0, kappa, dx_nm=0.1065, lam_nm=3.0, phi_gate=0.0, zeta=0.1, M=64,
                  tol=1e-8, check=True):

@@ -18,6 +18,11 @@ nanotube transistors, Sec. 3.1-3.3):
 * ``mixed_precision``   real-space (17,0), (26,0), (34,0), N = 1024, 4096 energies, a quarter
   of them within 20 meV of a lead subband edge.
 * ``serving_sweep``     256 self-consistent requests with Poisson arrivals.
+* ``gate_sweep``        zero-bias conductance against the gate voltage of a 10 nm (96-ring)
+  (17,0) mode-space channel, subbands j = 6, 5, V_GS from -1 to 2 V in 31 steps, each solve
+  started from the previous one's potential (the paper's sweep, Sec. 3.3-3.4).  The contact
+  Fermi level sits 1 eV below midgap (the paper's Pd contacts, Sec. 3.1): mu = -1 eV with
+  the leads at zero potential, so the contacts are metallic (p-type).
 """
 import numpy as np
 
@@ -124,3 +129,11 @@ def serving_sweep(n_requests=256, seed=5, rate=None):
     gaps = rng.exponential(1.0, n_requests)
     return dict(name="serving_sweep", n_tube=N_TUBE, t=T_HOP, kT=KT, eta=ETA, requests=reqs,
                 unit_gaps=gaps)
+
+
+def gate_sweep(N=96, n_points=31, v_lo=-1.0, v_hi=2.0, n_real=256, n_cont=64, mu=-1.0):
+    """Gate-voltage sweep at zero drain bias: a 96-ring (10.2 nm) channel, two subbands,
+    Gauss-Legendre real-axis energies on mu -+ 14 kT and a contour from E_B."""
+    return dict(name="gate_sweep", N=N, n_tube=N_TUBE, t=T_HOP, modes=(6, 5), kT=KT, eta=ETA,
+                mu=mu, V_DS=0.0, V_GS=np.linspace(v_lo, v_hi, n_points), n_real=n_real, n_cont=n_cont,
+                E_B=-3.0 * abs(T_HOP) - 1.0 - 0.5)

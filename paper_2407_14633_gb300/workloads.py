@@ -1,4 +1,4 @@
-"""Runners for the batched, mixed-precision and serving workloads through the C ABI
+"""Runners for the batched, mixed-precision, serving and gate-sweep workloads through the C ABI
 (used by bench.py --extras).  Timing uses the library's event-bracketed sweep time and host
 wall clock; inputs come from synth.py."""
 import time
@@ -248,3 +248,34 @@ def serving_sweep(n_requests=256, rate_factor=2.0, tol=1e-5, M=64):
             "saturated_bias_points_per_s": n_requests / sat_total, "saturated_steps": steps,
             "bitwise_same_as_sequential": same, "tol": tol,
             "mean_iterations": float(np.mean([r["iterations"] for r in served]))}
+
+
+def gate_sweep(w=None, tol=1e-8, M=64, warm=True):
+    """Zero-bias conductance against V_GS (Eq. zeroBiasG): per gate voltage one
+    self-consistent solve at V_DS = 0 (negf_sc_solve), started from the previous point's
+    potential when `warm` (the paper's sweep), then negf_conductance on the converged state.
+    Returns the conductances (S), iterations, and the points per second of the whole sweep."""
+    w = w or synth.gate_sweep()
+    N = w["N"]
+    with negf.Context() as ctx:
+        dev = ctx.device_create(N, block=1, rings_per_block=1, n_chains=len(w["modes"]))
+        ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], list(w["modes"]), 0.0, 0.0)
+        ctx.set_grid_spec(dev, w["mu"], w["mu"], w["kT"], w["eta"], w["E_B"], w["n_real"], w["n_cont"])
+        kappa = negf.poisson_kappa()
+        U0 = np.zeros(N)
+        G, iters, conv = [], [], []
+        t0 = time.perf_counter()
+        for v in w["V_GS"]:
+            r = ctx.sc_solve(dev, w["V_DS"], float(v), U0, kappa, M=M, tol=tol, check=False)
+            G.append(float(ctx.conductance([dev], w["mu"], w["kT"])[0]))
+            iters.append(r["iterations"])
+            conv.append(r["converged"])
+            if warm:
+                U0 = r["U"]
+        wall = time.perf_counter() - t0
+    lanes = len(w["modes"]) * (w["n_real"] + w["n_cont"])
+    # one NEGF evaluation per iteration plus the real-axis lanes of each conductance call
+    updates = N * (lanes * sum(iters) + len(w["modes"]) * w["n_real"] * len(G))
+    return {"V_GS": [float(v) for v in w["V_GS"]], "G_S": G, "iterations": iters, "converged": conv,
+            "points_per_s": len(G) / wall, "seconds": wall,
+            "ring_energy_mode_updates_per_s_wall": updates / wall}
