@@ -33,9 +33,13 @@ every `period` iterations (the paper uses 50); at such an iteration the peak is 
 the iteration's own potential on the grid in use, then the grid is rebuilt before the NEGF
 evaluation.
 
+Several channels (Sec. 2.3): their charge vectors are concatenated into one Broyden
+variable; a C x C coupling matrix K in the Poisson stand-in's source term couples the tubes.
+
 Parity: pinned (Thomas vs dense solve, closed-form solution for n = n0, Broyden vs the
 dense rank-one form, convergence on a linear map; the refining loop with a period beyond its
-iteration count against the plain loop on the refined grid).
+iteration count against the plain loop on the refined grid; the coupled Poisson against a dense
+block solve, two identical coupled tubes against one tube with kappa + kappa_x).
 """
 from dataclasses import dataclass
 import numpy as np
@@ -239,3 +243,64 @@ def sc_solve_adaptive(evaluate, integrand, make_grid, U0, n0, p, limits, a, b, k
         br.step(r["n"])
     return dict(converged=False, iterations=M, history=history, n=r["n"], n_in=br.n_in.copy(), U=U,
                 T=r["T"], I=r["I"], grid=grid, limits=limits, peaks=peaks)
+
+
+# ---- several channels sharing one Broyden vector (Sec. 2.3, the multi-channel extension)
+
+def poisson_solve_multi(n, n0, p, K):
+    """Poisson stand-in of C channels of equal length N, coupled through their charges:
+
+      U_c,i - U_G - r (U_c,i+1 - 2 U_c,i + U_c,i-1) = sum_c' K[c, c'] (n_c',i - n0_c',i),
+
+    Dirichlet U_c,-1 = U_S, U_c,N = U_D for every channel (shared contacts and gate).  K (C x C,
+    eV per electron per ring) replaces kappa: K[c, c] is a tube's own gate-screened coupling,
+    K[c, c'] the capacitive cross-coupling of two tubes at the same axial position (not in the
+    paper, whose 3D electrostatics couples the tubes; a builder-defined stand-in).  n, n0: (C, N).
+    """
+    n = np.asarray(n, dtype=np.float64)
+    q = np.asarray(K, dtype=np.float64) @ (n - np.asarray(n0))
+    U = np.zeros_like(n)
+    for c in range(n.shape[0]):
+        sub, dia, sup = poisson_system(n.shape[1], p)
+        rhs = p.U_G + q[c]
+        rhs[0] += p.r * p.U_S
+        rhs[-1] += p.r * p.U_D
+        U[c] = thomas(sub, dia, sup, rhs)
+    return U
+
+
+def poisson_charge_multi(U, n0, p, K):
+    """The charges (C, N) whose coupled Poisson solution is exactly U: per ring, K q = L with
+    L_c = (1 + 2r) U_c,i - r (U_c,i-1 + U_c,i+1) - U_G."""
+    U = np.asarray(U, dtype=np.float64)
+    r = p.r
+    L = np.zeros_like(U)
+    for c in range(U.shape[0]):
+        left = np.concatenate([[p.U_S], U[c, :-1]])
+        right = np.concatenate([U[c, 1:], [p.U_D]])
+        L[c] = (1.0 + 2.0 * r) * U[c] - r * (left + right) - p.U_G
+    return np.asarray(n0) + np.linalg.solve(np.asarray(K, dtype=np.float64), L)
+
+
+def sc_solve_multi(evaluates, U0, n0, p, K, zeta=0.1, M=64, tol=1e-8):
+    """Self-consistent loop of C channels with one Broyden vector n = (n^1, ..., n^C) (the
+    paper's multi-channel form of Alg. 3: the channel vectors are concatenated before the
+    Broyden step and split after it; eps_max and every dot product run over the whole vector).
+
+    evaluates[c](U_c) -> NEGF dict of channel c.  U0, n0: (C, N).  Returns converged,
+    iterations, history and per-channel n, U, T, I (lists).
+    """
+    C, N = np.asarray(U0).shape
+    br = Broyden(poisson_charge_multi(U0, n0, p, K).reshape(-1), zeta, M)
+    history = []
+    for it in range(M):
+        U = poisson_solve_multi(br.n_in.reshape(C, N), n0, p, K)
+        rs = [evaluates[c](U[c]) for c in range(C)]
+        n_out = np.concatenate([r["n"] for r in rs])
+        eps = residual(br.n_in, n_out)
+        history.append(eps)
+        done = eps < tol
+        if done or it == M - 1:
+            return dict(converged=bool(done), iterations=it + 1, history=history,
+                        n=[r["n"] for r in rs], U=list(U), T=[r["T"] for r in rs], I=[r["I"] for r in rs])
+        br.step(n_out)

@@ -234,3 +234,39 @@ def test_peak_pin_rejects(name, old, new):
         assert abs(np.sum(g["w"] * m["ring_integrand"](dev, U, g, 7)) - nr) > 1e-3 * nr, name
     else:
         assert peak_gap(m) > 0.0, name
+
+
+def coupled_poisson_gap(sc_mod):
+    """Miss of the coupled Poisson against a dense block solve (non-symmetric K)."""
+    from oracle import selfconsistent as real
+    rng = np.random.default_rng(5)
+    C, N = 3, 12
+    p = real.PoissonParams(kappa=0.0, lam_nm=2.0, U_G=-0.2, U_S=0.05, U_D=-0.3)
+    K = np.array([[19.0, 2.0, 0.3], [1.1, 17.5, 2.4], [0.2, 2.9, 18.2]])
+    n0 = rng.uniform(1.5, 2.5, (C, N))
+    n = n0 + rng.normal(0, 0.01, (C, N))
+    r = p.r
+    T = np.diag(np.full(N, 1 + 2 * r)) + np.diag(np.full(N - 1, -r), 1) + np.diag(np.full(N - 1, -r), -1)
+    want = []
+    for c in range(C):
+        b = p.U_G + sum(K[c, d] * (n[d] - n0[d]) for d in range(C))
+        b[0] += r * p.U_S
+        b[-1] += r * p.U_D
+        want.append(np.linalg.solve(T, b))
+    return float(np.max(np.abs(sc_mod["poisson_solve_multi"](n, n0, p, K) - np.array(want))))
+
+
+def test_real_coupled_poisson_passes_its_pin():
+    from oracle import selfconsistent as s
+    assert coupled_poisson_gap(vars(s)) < 1e-12
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("coupling matrix transposed", "q = np.asarray(K, dtype=np.float64) @ (n - np.asarray(n0))",
+     "q = np.asarray(K, dtype=np.float64).T @ (n - np.asarray(n0))"),
+    ("cross-coupling dropped", "q = np.asarray(K, dtype=np.float64) @ (n - np.asarray(n0))",
+     "q = np.diag(np.diag(np.asarray(K, dtype=np.float64))) @ (n - np.asarray(n0))"),
+])
+def test_coupled_poisson_pin_rejects(name, old, new):
+    m = mutant("selfconsistent", old, new)
+    assert coupled_poisson_gap(m) > 1e-6, name

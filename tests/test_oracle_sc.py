@@ -128,3 +128,75 @@ def test_refinement_period_and_peak_count():
     r = sc.sc_solve_adaptive(ev, integ, make, U0, n0, p, (-0.3, -0.2), 3.0, 1.0, kT, period=3, M=20, tol=1e-9)
     assert len(r["peaks"]) == 1 + (r["iterations"] - 1) // 3
     assert r["grid"]["E_l1"] == max(r["limits"][0], r["grid"]["E_min"])
+
+
+# ---- several channels with one Broyden vector (Sec. 2.3)
+
+def test_coupled_poisson_matches_dense_block_solve():
+    rng = np.random.default_rng(3)
+    C, N = 3, 30
+    p = sc.PoissonParams(kappa=0.0, lam_nm=2.0, U_G=-0.2, U_S=0.05, U_D=-0.3)
+    K = np.array([[19.0, 2.0, 0.3], [1.1, 17.5, 2.4], [0.2, 2.9, 18.2]])   # not symmetric: orientation shows
+    n0 = rng.uniform(1.5, 2.5, (C, N))
+    n = n0 + rng.normal(0, 0.01, (C, N))
+    r = p.r
+    A = np.zeros((C * N, C * N))
+    b = np.zeros(C * N)
+    for c in range(C):
+        for i in range(N):
+            row = c * N + i
+            A[row, row] = 1 + 2 * r
+            if i > 0:
+                A[row, row - 1] = -r
+            if i < N - 1:
+                A[row, row + 1] = -r
+            b[row] = p.U_G + sum(K[c, d] * (n[d, i] - n0[d, i]) for d in range(C))
+            b[row] += r * p.U_S if i == 0 else 0.0
+            b[row] += r * p.U_D if i == N - 1 else 0.0
+    U = sc.poisson_solve_multi(n, n0, p, K)
+    assert np.max(np.abs(U.reshape(-1) - np.linalg.solve(A, b))) < 1e-12
+    back = sc.poisson_charge_multi(U, n0, p, K)
+    assert np.max(np.abs(back - n)) < 1e-10
+
+
+def _tube(N, V_DS, modes, n_real=40, n_cont=12):
+    dev = mdl.cnt_build("mode", 17, -2.7, N, 0.0, -V_DS, modes=modes)
+    g = q.bias_grid(0.0, -V_DS, 0.025, n_real, n_cont, -10.0, 1e-6)
+    return dev, g, chg.neutral_charge(dev, n_cont, -10.0)
+
+
+def test_two_identical_coupled_tubes_iterate_like_one_tube():
+    # identical tubes under K = [[k, kx], [kx, k]] carry equal charges, so each sees
+    # (k + kx)(n - n0): the concatenated Broyden vector [x; x] gives the iterates of x (every
+    # norm and dot product doubles, and V = df / ||df||^2 halves), so the two-tube loop is the
+    # one-tube loop with kappa = k + kx, iteration by iteration
+    N, V_DS, V_GS = 16, 0.2, 0.1
+    dev, g, n0 = _tube(N, V_DS, (6,))
+    k, kx = sc.kappa_from_geometry(), 3.0
+    U0 = np.linspace(0.0, -V_DS, N) + 0.03 * np.cos(np.arange(N))
+    ev = lambda U: chg.negf_evaluate(dev, U, g)
+    p1 = sc.PoissonParams(kappa=k + kx, U_G=-V_GS, U_S=0.0, U_D=-V_DS)
+    one = sc.sc_solve(ev, U0, n0, p1, M=64, tol=1e-10)
+    p2 = sc.PoissonParams(kappa=0.0, U_G=-V_GS, U_S=0.0, U_D=-V_DS)
+    two = sc.sc_solve_multi([ev, ev], np.array([U0, U0]), np.array([n0, n0]), p2, [[k, kx], [kx, k]], M=64, tol=1e-10)
+    assert one["converged"] and two["converged"] and one["iterations"] == two["iterations"]
+    assert np.max(np.abs(np.array(one["history"]) - np.array(two["history"]))) < 1e-9 * max(one["history"])
+    for c in range(2):
+        assert np.max(np.abs(two["n"][c] - one["n"])) < 1e-12 * np.max(one["n"])
+        assert np.max(np.abs(two["U"][c] - one["U"])) < 1e-10
+
+
+def test_uncoupled_tubes_reach_their_own_fixed_points():
+    N, V_DS, V_GS = 14, 0.2, -0.1
+    tubes = [_tube(N, V_DS, m) for m in ((6,), (5,), (6, 5))]
+    k = sc.kappa_from_geometry()
+    U0 = np.tile(np.linspace(0.0, -V_DS, N), (3, 1))
+    evs = [(lambda d, g: (lambda U: chg.negf_evaluate(d, U, g)))(d, g) for d, g, _ in tubes]
+    p = sc.PoissonParams(kappa=0.0, U_G=-V_GS, U_S=0.0, U_D=-V_DS)
+    multi = sc.sc_solve_multi(evs, U0, np.array([t[2] for t in tubes]), p, np.diag([k, k, k]), M=64, tol=1e-11)
+    assert multi["converged"]
+    for c, (d, g, n0) in enumerate(tubes):
+        single = sc.sc_solve(evs[c], U0[c], n0, sc.PoissonParams(kappa=k, U_G=-V_GS, U_S=0.0, U_D=-V_DS),
+                             M=64, tol=1e-11)
+        assert single["converged"]
+        assert np.max(np.abs(multi["n"][c] - single["n"])) < 1e-8 * np.max(single["n"])
