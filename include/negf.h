@@ -197,6 +197,49 @@ int negf_make_grid(const negf_grid_spec* spec, double* E, double* w, double* fS,
 /* Build the default grid and set it on a device. */
 int negf_set_grid_spec(negf_ctx* ctx, int dev, const negf_grid_spec* spec);
 
+/* ---- semi-adaptive real-axis grid (Sec. 3.3) ---------------------------------------------- */
+
+/* The real-axis path [E_min, E_max] split at E_l1 <= E_l2 into three sub-intervals, each with
+ * its own Gauss-Legendre rule of ceil(density * width / kT - 1e-6) points (at least one; none
+ * for an empty sub-interval).  The limits are clipped into [E_min, E_max].  Refinement locates
+ * the peak E_s of the charge integrand of one ring (the van Hove singularity that sharpens
+ * with channel length) and moves the limits to E_l1 = E_s - a kT, E_l2 = E_s + b kT (the paper
+ * uses a = 3, b = 1).  In a self-consistent session (negf_sc_begin on a device whose grid was
+ * set with negf_set_grid_adaptive) the limits are refined at the first iteration and at every
+ * iteration that is a multiple of `period` (the paper uses 50; 0 = the first only), with that
+ * iteration's potential, before its NEGF evaluation.  ring: the ring whose integrand is used
+ * (-1 = the centre ring n_rings / 2). */
+typedef struct {
+  double E_l1, E_l2;
+  double density[3];
+  double a, b;
+  int period;
+  int ring;
+} negf_adaptive;
+
+/* Host helper: the grid of spec with the semi-adaptive real axis (spec->n_real and spec->rule
+ * are ignored; the contour, E_min, E_max and occupations follow spec as in negf_make_grid).
+ * *n_real receives the number of real-axis nodes; E, w, fS, fD may be NULL to count only,
+ * else they need *n_real doubles each (call once with NULL to size them).  z, c as in
+ * negf_make_grid (NULL when spec->n_cont = 0 or when counting). */
+int negf_make_grid_adaptive(const negf_grid_spec* spec, const negf_adaptive* ad, int* n_real, double* E,
+                            double* w, double* fS, double* fD, double* z, double* c);
+/* Set the semi-adaptive grid on a device (it then also serves negf_sc_begin like
+ * negf_set_grid_spec).  Any later negf_set_grid / negf_set_grid_spec replaces it. */
+int negf_set_grid_adaptive(negf_ctx* ctx, int dev, const negf_grid_spec* spec, const negf_adaptive* ad);
+/* Charge integrand of one ring at every real-axis node of the device's grid, with the device's
+ * current potential (host output, n_real doubles):
+ *   I_r(E_k) = sum_chains (g_s g_b / 2 pi) [fS_k Tr_r A_S(E_k) + fD_k Tr_r A_D(E_k)],
+ * so that sum_k w_k I_r(E_k) is the real-axis part of n_r.  One lane per energy. */
+int negf_ring_integrand(negf_ctx* ctx, int dev, int ring, double* I);
+/* Refine a semi-adaptive grid once: E_s = the node of largest integrand (the first on ties)
+ * of the refinement ring, then the grid rebuilt with E_l1 = E_s - a kT, E_l2 = E_s + b kT.
+ * E_s may be NULL.  NEGF_EINVAL if the device grid is not semi-adaptive. */
+int negf_refine_grid(negf_ctx* ctx, int dev, double* E_s);
+/* Current grid sizes, and the current (clipped) limits of a semi-adaptive grid (NaN for other
+ * grids).  Any pointer may be NULL.  Valid during a self-consistent session. */
+int negf_grid_info(negf_ctx* ctx, int dev, int* n_real, int* n_cont, double* E_l1, double* E_l2);
+
 /* ---- one NEGF evaluation ----------------------------------------------------------------- */
 
 /* Outputs of one device.  n (n_rings, required): electron count per ring.  T (n_real,
@@ -318,6 +361,27 @@ int negf_sc_get_state(negf_ctx* ctx, int dev, double* n_in, double* n_in_old, do
                       double* V, double* W, int* m);
 int negf_sc_set_state(negf_ctx* ctx, int dev, const double* n_in, const double* n_in_old,
                       const double* f_old, const double* V, const double* W, int m);
+
+/* Self-consistent solve of C channels with one Broyden vector (Sec. 2.3: the charge vectors
+ * of several channel materials are concatenated, n = (n^1, ..., n^C), so eps_max and every
+ * dot product of Alg. 3 run over all channels).  The channels are the devices devs[0..C-1]
+ * (1 <= C <= 64), tubes of equal n_rings sharing contacts and gate, each with its grid set
+ * from a grid spec (negf_set_grid_spec; a semi-adaptive grid is used as it stands, without
+ * refinement).  Their Poisson stand-ins are coupled through the C x C row-major matrix K (eV
+ * per electron per ring), which replaces pois->kappa:
+ *   U_c,i - U_G - (lam/dx)^2 (U_c,i+1 - 2 U_c,i + U_c,i-1) = sum_c' K[c][c'] (n_c',i - n0_c',i)
+ * (K[c][c] a tube's own gate-screened coupling, e.g. negf_poisson_kappa; K[c][c'] the
+ * capacitive cross-coupling of two tubes at the same ring position: a stand-in for the
+ * paper's 3D electrostatics, which couples the tubes through the shared field).  U0: C x
+ * n_rings starting potentials (the loop starts from the charges whose coupled Poisson
+ * solution is U0; K must be invertible).  All channels' sweeps run in one batched launch per
+ * iteration, captured as one CUDA graph.  res: C results (n, U, T per channel; history,
+ * iterations and converged are shared).  Returns NEGF_ENOTCONVERGED (results filled) if M
+ * evaluations pass without eps_max < tol; NEGF_EINVAL for unequal ring counts, a device
+ * listed twice, a singular or non-finite K. */
+int negf_sc_solve_multi(negf_ctx* ctx, const int* devs, int n_channels, const negf_bias* bias,
+                        const negf_poisson* pois, const double* K, const negf_broyden* br,
+                        const double* U0, negf_sc_result* res);
 
 /* ---- serving: continuous batching of self-consistent solves ----------------------------- */
 

@@ -17,7 +17,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnegf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: no fused multiply-add contraction, so host arithmetic (grids, point counts) gives
+# the same bits on x86-64 and on Arm, where the compiler would otherwise fuse by default
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+         "-Xcompiler", "-ffp-contract=off",
          "-I" + os.path.join(ROOT, "include")]
 
 

@@ -374,6 +374,41 @@ double fermi_real(double x, double kT) {
 
 }  // namespace
 
+namespace negf {
+void gl_rule(int n, std::vector<double>& x, std::vector<double>& w) { gauss_legendre(n, x, w); }
+double fermi_host(double x, double kT) { return fermi_real(x, kT); }
+
+// negf_set_grid without the session check (the semi-adaptive grid is rebuilt inside a
+// self-consistent session)
+int set_grid_internal(Ctx* c, Dev* d, const negf_grid* g) {
+  if (!g || g->n_real < 0 || g->n_cont < 0 || g->n_real + g->n_cont == 0 || !(g->eta >= 0.0))
+    return set_err(c, NEGF_EINVAL, "bad grid");
+  if (g->n_real > 0 && (!g->E || !g->w || !g->fS || !g->fD)) return set_err(c, NEGF_EINVAL, "null real-axis grid array");
+  if (g->n_cont > 0 && (!g->z || !g->c)) return set_err(c, NEGF_EINVAL, "null contour array");
+  for (int k = 0; k < g->n_cont; ++k)
+    if (!(g->z[2 * k + 1] > 0.0)) return set_err(c, NEGF_EINVAL, "contour node not in the upper half plane");
+  if (g->n_real > 0 && !(g->eta > 0.0)) return set_err(c, NEGF_EINVAL, "real-axis energies need eta > 0");
+  cudaSetDevice(c->ordinal);
+  int rc;
+  const size_t nr = std::max(g->n_real, 1), nc = std::max(g->n_cont, 1);
+  std::vector<double> zero(2 * std::max(nr, nc), 0.0);
+  if ((rc = upload(c, d->dE, g->n_real ? g->E : zero.data(), nr * 8))) return rc;
+  if ((rc = upload(c, d->dw, g->n_real ? g->w : zero.data(), nr * 8))) return rc;
+  if ((rc = upload(c, d->dfS, g->n_real ? g->fS : zero.data(), nr * 8))) return rc;
+  if ((rc = upload(c, d->dfD, g->n_real ? g->fD : zero.data(), nr * 8))) return rc;
+  if ((rc = upload(c, d->dz, g->n_cont ? g->z : zero.data(), nc * 16))) return rc;
+  if ((rc = upload(c, d->dc, g->n_cont ? g->c : zero.data(), nc * 16))) return rc;
+  d->n_real = g->n_real;
+  d->n_cont = g->n_cont;
+  d->eta = g->eta;
+  d->hE.assign(g->E, g->E + g->n_real);
+  d->grid_set = true;
+  d->spec_set = false;
+  d->adaptive = false;
+  return NEGF_OK;
+}
+}  // namespace negf
+
 // =====================================================================================
 extern "C" {
 
@@ -451,6 +486,7 @@ int negf_destroy(negf_ctx* c) {
   free_plan_bufs(c, c->scratch);
   c->arena.release(c->lane_stats);
   c->arena.release(c->cond);
+  c->arena.release(c->refine);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return NEGF_OK;
@@ -656,30 +692,7 @@ int negf_set_grid(negf_ctx* c, int dev, const negf_grid* g) {
   Dev* d = get_dev(c, dev);
   if (!d) return set_err(c, NEGF_ENOTFOUND, "unknown device");
   NEGF_NOT_IN_SESSION(c, d);
-  if (!g || g->n_real < 0 || g->n_cont < 0 || g->n_real + g->n_cont == 0 || !(g->eta >= 0.0))
-    return set_err(c, NEGF_EINVAL, "bad grid");
-  if (g->n_real > 0 && (!g->E || !g->w || !g->fS || !g->fD)) return set_err(c, NEGF_EINVAL, "null real-axis grid array");
-  if (g->n_cont > 0 && (!g->z || !g->c)) return set_err(c, NEGF_EINVAL, "null contour array");
-  for (int k = 0; k < g->n_cont; ++k)
-    if (!(g->z[2 * k + 1] > 0.0)) return set_err(c, NEGF_EINVAL, "contour node not in the upper half plane");
-  if (g->n_real > 0 && !(g->eta > 0.0)) return set_err(c, NEGF_EINVAL, "real-axis energies need eta > 0");
-  cudaSetDevice(c->ordinal);
-  int rc;
-  const size_t nr = std::max(g->n_real, 1), nc = std::max(g->n_cont, 1);
-  std::vector<double> zero(2 * std::max(nr, nc), 0.0);
-  if ((rc = upload(c, d->dE, g->n_real ? g->E : zero.data(), nr * 8))) return rc;
-  if ((rc = upload(c, d->dw, g->n_real ? g->w : zero.data(), nr * 8))) return rc;
-  if ((rc = upload(c, d->dfS, g->n_real ? g->fS : zero.data(), nr * 8))) return rc;
-  if ((rc = upload(c, d->dfD, g->n_real ? g->fD : zero.data(), nr * 8))) return rc;
-  if ((rc = upload(c, d->dz, g->n_cont ? g->z : zero.data(), nc * 16))) return rc;
-  if ((rc = upload(c, d->dc, g->n_cont ? g->c : zero.data(), nc * 16))) return rc;
-  d->n_real = g->n_real;
-  d->n_cont = g->n_cont;
-  d->eta = g->eta;
-  d->hE.assign(g->E, g->E + g->n_real);
-  d->grid_set = true;
-  d->spec_set = false;
-  return NEGF_OK;
+  return set_grid_internal(c, d, g);
 }
 
 int negf_make_grid(const negf_grid_spec* s, double* E, double* w, double* fS, double* fD, double* z,

@@ -80,6 +80,11 @@ struct Dev {
   DBuf dU, dE, dw, dfS, dfD, dz, dc, dgb;
   DBuf dn, dnr, dnc, dT, dI;
   ScSession* sc = nullptr;   // active self-consistent session (sc.cu)
+  // semi-adaptive real-axis grid (adaptive.cu): settings, current clipped limits, segment sizes
+  bool adaptive = false;
+  negf_adaptive ad{};
+  double l1 = 0.0, l2 = 0.0;
+  int seg[3] = {0, 0, 0};
 };
 
 struct Ctx {
@@ -102,6 +107,7 @@ struct Ctx {
   uint64_t prof_count = 0;
   DBuf lane_stats;   // 4 counters of negf_sweep_lanes
   DBuf cond;         // descriptors and outputs of negf_conductance
+  DBuf refine;       // unit weights and the located peak of the semi-adaptive grid
   // launch shapes (CTA width, resident CTAs per SM) chosen by the autotuner of the
   // wide-block sweep, keyed by (element type, b, m, items); the latest per (type, b, m)
   std::map<std::tuple<int, int, int, int>, std::pair<int, int>> blk_tuned;
@@ -114,6 +120,12 @@ struct Ctx {
 struct Serve;
 void serve_free(Ctx* c);
 int set_err(Ctx* c, int code, const std::string& msg);
+int set_grid_internal(Ctx* c, Dev* d, const negf_grid* g);
+void gl_rule(int n, std::vector<double>& x, std::vector<double>& w);
+double fermi_host(double x, double kT);
+// semi-adaptive grid (adaptive.cu): peak of the refinement ring's integrand with the device's
+// current potential and grid, then the grid rebuilt around it
+int refine_grid_internal(Ctx* c, Dev* d, double* E_s);
 bool ensure(Ctx* c, DBuf& b, size_t bytes);
 int upload(Ctx* c, DBuf& b, const void* src, size_t bytes);
 

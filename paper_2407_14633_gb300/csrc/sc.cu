@@ -23,6 +23,7 @@ struct ScSession {
   int* h_state = nullptr;
   int iterations = 0;
   int last_state = 0;
+  int refines = 0;
   uint64_t kernels_per_iter = 0;
 };
 
@@ -38,6 +39,54 @@ void sc_session_free(Ctx* c, Dev* d) {
   free_plan_bufs(c, s->bufs);
   delete s;
   d->sc = nullptr;
+}
+
+// Capture one iteration -- Poisson, the plan's sweeps and second stage, Broyden -- as a CUDA
+// graph (left uncaptured if the stream cannot be captured; the iteration then launches directly).
+static void capture_iteration(Ctx* c, ScSession* s) {
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  s->exec = nullptr;
+  s->graph = nullptr;
+  s->kernels_per_iter = 3;
+  for (int g = 0; g < NGROUPS; ++g) s->kernels_per_iter += (s->plan.ncls[g] > 0);
+  const ScDev* dsc = (const ScDev*)s->sc.p;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+    const uint64_t l0 = c->launches;
+    const bool ok = launch_poisson(dsc, 1, c->stream) == 0 && launch_plan(c, s->plan) == NEGF_OK &&
+                    launch_broyden(dsc, 1, c->stream) == 0;
+    c->launches = l0;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(c->stream, &g) == cudaSuccess && ok && cudaGraphInstantiate(&s->exec, g, 0) == cudaSuccess)
+      s->graph = g;
+    else if (g)
+      cudaGraphDestroy(g);
+    cudaGetLastError();
+  }
+}
+
+// An iteration that refines a semi-adaptive grid (Sec. 3.3): Poisson, then the peak of the
+// refinement ring's integrand with the new potential on the grid in use, the grid rebuilt
+// around it, a new plan and graph, then the NEGF evaluation and Broyden step on the new grid.
+// A session that has already stopped (converged or out of history) is left as it is.
+static int refine_iteration(Ctx* c, Dev* d, ScSession* s) {
+  const ScDev* dsc = (const ScDev*)s->sc.p;
+  if (cudaMemcpyAsync(s->h_state, s->state.p, 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return set_err(c, NEGF_ECUDA, "self-consistent iteration failed");
+  if (*s->h_state != 0) return NEGF_OK;
+  if (launch_poisson(dsc, 1, c->stream)) return set_err(c, NEGF_ECUDA, "poisson launch failed");
+  ++c->launches;
+  int rc = refine_grid_internal(c, d, nullptr);
+  if (rc) return rc;
+  ++s->refines;
+  std::vector<Dev*> one{d};
+  if ((rc = build_plan(c, one, nullptr, -1, s->plan, &s->bufs))) return rc;
+  capture_iteration(c, s);
+  if ((rc = launch_plan(c, s->plan))) return rc;
+  if (launch_broyden(dsc, 1, c->stream)) return set_err(c, NEGF_ECUDA, "broyden launch failed");
+  ++c->launches;
+  return NEGF_OK;
 }
 
 static int run_iteration(Ctx* c, ScSession* s) {
@@ -141,22 +190,9 @@ int negf_sc_begin(negf_ctx* c, int dev, const negf_bias* bias, const negf_poisso
   if (cudaMemcpy(s->sc.p, &sd, sizeof(sd), cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(set_err(c, NEGF_ECUDA, "upload failed"));
   if (cudaMallocHost(&s->h_state, sizeof(int)) != cudaSuccess) return fail(set_err(c, NEGF_ENOMEM, "pinned alloc failed"));
-  s->kernels_per_iter = 3;
-  for (int g = 0; g < NGROUPS; ++g) s->kernels_per_iter += (s->plan.ncls[g] > 0);
-  // capture one iteration (falls back to direct launches if the stream cannot be captured)
-  const ScDev* dsc = (const ScDev*)s->sc.p;
-  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-    const uint64_t l0 = c->launches;
-    const bool ok = launch_poisson(dsc, 1, c->stream) == 0 && launch_plan(c, s->plan) == NEGF_OK &&
-                    launch_broyden(dsc, 1, c->stream) == 0;
-    c->launches = l0;
-    cudaGraph_t g = nullptr;
-    if (cudaStreamEndCapture(c->stream, &g) == cudaSuccess && ok && cudaGraphInstantiate(&s->exec, g, 0) == cudaSuccess)
-      s->graph = g;
-    else if (g)
-      cudaGraphDestroy(g);
-    cudaGetLastError();
-  }
+  // capture one iteration (a semi-adaptive grid is refined at the first iteration, which
+  // captures its own graph)
+  if (!d->adaptive) capture_iteration(c, s);
   return NEGF_OK;
 }
 
@@ -170,7 +206,9 @@ int negf_sc_step(negf_ctx* c, int dev, int k, int* state) {
   cudaSetDevice(c->ordinal);
   for (int i = 0; i < k; ++i) {
     if (s->last_state != 0) break;
-    int rc = run_iteration(c, s);
+    const int it = s->iterations;
+    const bool refine = d->adaptive && (it == 0 || (d->ad.period > 0 && it % d->ad.period == 0));
+    int rc = refine ? refine_iteration(c, d, s) : run_iteration(c, s);
     if (rc) return rc;
     if (state) {
       if (cudaMemcpyAsync(s->h_state, s->state.p, 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||

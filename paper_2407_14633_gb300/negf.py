@@ -44,6 +44,11 @@ class GridSpec(C.Structure):
                 ("f2", C.c_double), ("n_real", C.c_int), ("n_cont", C.c_int), ("rule", C.c_int)]
 
 
+class Adaptive(C.Structure):
+    _fields_ = [("E_l1", C.c_double), ("E_l2", C.c_double), ("density", C.c_double * 3), ("a", C.c_double),
+                ("b", C.c_double), ("period", C.c_int), ("ring", C.c_int)]
+
+
 class Out(C.Structure):
     _fields_ = [("n", C.c_void_p), ("T", C.c_void_p), ("I", C.c_void_p), ("n_cont", C.c_void_p),
                 ("n_real_part", C.c_void_p), ("flags", C.c_void_p), ("resid", C.c_void_p),
@@ -97,10 +102,18 @@ _PROTOS = {
     "negf_sample_lanes": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip, _dp, _dp, C.c_int, _ip, _dp]),
     "negf_neutral_charge": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, _dp]),
     "negf_conductance": (C.c_int, [C.c_void_p, _ip, C.c_int, C.c_double, C.c_double, _dp, _dp]),
+    "negf_make_grid_adaptive": (C.c_int, [C.POINTER(GridSpec), C.POINTER(Adaptive), _ip, _dp, _dp, _dp, _dp, _dp,
+                                          _dp]),
+    "negf_set_grid_adaptive": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(GridSpec), C.POINTER(Adaptive)]),
+    "negf_ring_integrand": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp]),
+    "negf_refine_grid": (C.c_int, [C.c_void_p, C.c_int, _dp]),
+    "negf_grid_info": (C.c_int, [C.c_void_p, C.c_int, _ip, _ip, _dp, _dp]),
     "negf_poisson_kappa": (C.c_double, [C.c_double, C.c_double, C.c_double, C.c_double]),
     "negf_sc_solve": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Bias), C.POINTER(Poisson), C.POINTER(Broyden),
                                 _dp, C.POINTER(ScResult)]),
     "negf_launch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
+    "negf_sc_solve_multi": (C.c_int, [C.c_void_p, _ip, C.c_int, C.POINTER(Bias), C.POINTER(Poisson), _dp,
+                                      C.POINTER(Broyden), _dp, C.c_void_p]),
     "negf_sc_begin": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Bias), C.POINTER(Poisson), C.POINTER(Broyden), _dp]),
     "negf_sc_step": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip]),
     "negf_sc_end": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(ScResult)]),
@@ -187,6 +200,31 @@ def make_grid(mu_S, mu_D, kT, eta, E_B, n_real, n_cont, rule=RULE_GAUSS, E_min=f
     zc = z.view(np.complex128)[:n_cont]
     cc = c.view(np.complex128)[:n_cont]
     return dict(E=E[:n_real], w=w[:n_real], fS=fS[:n_real], fD=fD[:n_real], z=zc, c=cc, eta=eta)
+
+
+def _adaptive(E_l1, E_l2, densities, a, b, period, ring):
+    return Adaptive(E_l1, E_l2, (C.c_double * 3)(*densities), a, b, period, ring)
+
+
+def make_grid_adaptive(mu_S, mu_D, kT, eta, E_B, n_cont, E_l1, E_l2, densities, a=3.0, b=1.0,
+                       E_min=float("nan"), E_max=float("nan"), f1=float("nan"), f2=float("nan")):
+    """negf_make_grid_adaptive: the semi-adaptive grid of a bias point (host arrays)."""
+    lib = load()
+    s = GridSpec(mu_S, mu_D, kT, eta, E_B, E_min, E_max, f1, f2, 0, n_cont, RULE_GAUSS)
+    ad = _adaptive(E_l1, E_l2, densities, a, b, 0, -1)
+    n = C.c_int()
+    rc = lib.negf_make_grid_adaptive(C.byref(s), C.byref(ad), C.byref(n), None, None, None, None, None, None)
+    if rc:
+        raise NegfError(rc, "make_grid_adaptive")
+    nr = n.value
+    E, w, fS, fD = (np.zeros(nr) for _ in range(4))
+    z = np.zeros(2 * max(n_cont, 1))
+    c = np.zeros(2 * max(n_cont, 1))
+    rc = lib.negf_make_grid_adaptive(C.byref(s), C.byref(ad), C.byref(n), _p(E), _p(w), _p(fS), _p(fD), _p(z),
+                                     _p(c))
+    if rc:
+        raise NegfError(rc, "make_grid_adaptive")
+    return dict(E=E, w=w, fS=fS, fD=fD, z=z.view(np.complex128)[:n_cont], c=c.view(np.complex128)[:n_cont], eta=eta)
 
 
 def poisson_kappa(eps_r=3.9, d_nm=1.3, t_ox_nm=10.0, dx_nm=0.1065):
@@ -282,12 +320,46 @@ class Context:
         g = Grid(E.size, _p(E), _p(w), _p(fS), _p(fD), eta, zz.size // 2, _p(zz), _p(cc))
         self._chk(self.lib.negf_set_grid(self.h, dev, C.byref(g)))
         self._dev[dev]["n_real"] = E.size
+        self._dev[dev].pop("n_real_max", None)
 
     def set_grid_spec(self, dev, mu_S, mu_D, kT, eta, E_B, n_real, n_cont, rule=RULE_GAUSS,
                       E_min=float("nan"), E_max=float("nan"), f1=float("nan"), f2=float("nan")):
         s = GridSpec(mu_S, mu_D, kT, eta, E_B, E_min, E_max, f1, f2, n_real, n_cont, rule)
         self._chk(self.lib.negf_set_grid_spec(self.h, dev, C.byref(s)))
         self._dev[dev]["n_real"] = n_real
+        self._dev[dev].pop("n_real_max", None)
+
+    def set_grid_adaptive(self, dev, mu_S, mu_D, kT, eta, E_B, n_cont, E_l1, E_l2, densities, a=3.0, b=1.0,
+                          period=50, ring=-1, E_min=float("nan"), E_max=float("nan")):
+        """negf_set_grid_adaptive: the semi-adaptive real-axis grid (Sec. 3.3) on a device."""
+        s = GridSpec(mu_S, mu_D, kT, eta, E_B, E_min, E_max, float("nan"), float("nan"), 0, n_cont, RULE_GAUSS)
+        self._chk(self.lib.negf_set_grid_adaptive(self.h, dev, C.byref(s),
+                                                  C.byref(_adaptive(E_l1, E_l2, densities, a, b, period, ring))))
+        info = self.grid_info(dev)
+        lo = min(mu_S, mu_D) - 14.0 * kT if E_min != E_min else E_min
+        hi = max(mu_S, mu_D) + 14.0 * kT if E_max != E_max else E_max
+        # room for any refined grid: each segment holds at most density * window / kT + 1 points
+        self._dev[dev].update(n_real=info["n_real"],
+                              n_real_max=int(sum(np.ceil(d * (hi - lo) / kT) + 1 for d in densities)))
+        return info
+
+    def grid_info(self, dev):
+        nr, nc = C.c_int(), C.c_int()
+        l1, l2 = C.c_double(), C.c_double()
+        self._chk(self.lib.negf_grid_info(self.h, dev, C.byref(nr), C.byref(nc), C.byref(l1), C.byref(l2)))
+        return dict(n_real=nr.value, n_cont=nc.value, E_l1=l1.value, E_l2=l2.value)
+
+    def ring_integrand(self, dev, ring):
+        out = np.zeros(max(self.grid_info(dev)["n_real"], 1))
+        self._chk(self.lib.negf_ring_integrand(self.h, dev, ring, _p(out)))
+        return out
+
+    def refine_grid(self, dev):
+        """negf_refine_grid: returns the located peak E_s; the device grid is rebuilt around it."""
+        e = C.c_double()
+        self._chk(self.lib.negf_refine_grid(self.h, dev, C.byref(e)))
+        self._dev[dev]["n_real"] = self.grid_info(dev)["n_real"]
+        return e.value
 
     # ---- evaluation
     def compute(self, devs):
@@ -374,7 +446,7 @@ class Context:
     def sc_solve(self, dev, V_DS, V_GS, U0, kappa, dx_nm=0.1065, lam_nm=3.0, phi_gate=0.0, zeta=0.1, M=64,
                  tol=1e-8, check=True):
         N = self._dev[dev]["n_rings"]
-        nr = self._dev[dev].get("n_real", 0)
+        nr = self._dev[dev].get("n_real_max", self._dev[dev].get("n_real", 0))
         n, U, T, hist = np.zeros(N), np.zeros(N), np.zeros(max(nr, 1)), np.zeros(M)
         r = ScResult(_p(n), _p(U), _p(T), _p(hist), 0.0, 0, 0)
         u0 = _f64(U0, N)
@@ -383,8 +455,35 @@ class Context:
                                     C.byref(Broyden(zeta, M, tol)), _p(u0), C.byref(r))
         if rc not in (OK, ENOTCONVERGED) or (check and rc):
             self._chk(rc)
+        nr = self._dev[dev]["n_real"] = self.grid_info(dev)["n_real"]
         return dict(status=rc, n=n, U=U, T=T[:nr], history=hist[:r.iterations], I=r.I,
                     converged=bool(r.converged), iterations=r.iterations)
+
+    def sc_solve_multi(self, devs, V_DS, V_GS, U0, K, dx_nm=0.1065, lam_nm=3.0, phi_gate=0.0, zeta=0.1, M=64,
+                       tol=1e-8, check=True):
+        """negf_sc_solve_multi: C coupled channels with one Broyden vector; U0 (C, N), K (C, C)."""
+        devs = list(devs)
+        Cn = len(devs)
+        N = self._dev[devs[0]]["n_rings"]
+        u0 = _f64(U0, Cn * N)
+        k = _f64(K, Cn * Cn)
+        arrs = []
+        res = (ScResult * Cn)()
+        for i, d in enumerate(devs):
+            nr = self._dev[d].get("n_real", 0)
+            a = dict(n=np.zeros(N), U=np.zeros(N), T=np.zeros(max(nr, 1)), history=np.zeros(M), nr=nr)
+            arrs.append(a)
+            res[i] = ScResult(_p(a["n"]), _p(a["U"]), _p(a["T"]), _p(a["history"]), 0.0, 0, 0)
+        ids = np.ascontiguousarray(devs, dtype=np.int32)
+        rc = self.lib.negf_sc_solve_multi(self.h, _pi(ids), Cn, C.byref(Bias(V_DS, V_GS)),
+                                          C.byref(Poisson(0.0, dx_nm, lam_nm, phi_gate)), _p(k),
+                                          C.byref(Broyden(zeta, M, tol)), _p(u0), res)
+        if rc not in (OK, ENOTCONVERGED) or (check and rc):
+            self._chk(rc)
+        it = res[0].iterations
+        return dict(status=rc, converged=bool(res[0].converged), iterations=it, history=arrs[0]["history"][:it],
+                    n=[a["n"] for a in arrs], U=[a["U"] for a in arrs], T=[a["T"][:a["nr"]] for a in arrs],
+                    I=[res[i].I for i in range(Cn)])
 
     def sc_begin(self, dev, V_DS, V_GS, U0, kappa, dx_nm=0.1065, lam_nm=3.0, phi_gate=0.0, zeta=0.1, M=64,
                  tol=1e-8):
@@ -401,13 +500,14 @@ class Context:
 
     def sc_end(self, dev, check=False):
         N = self._dev[dev]["n_rings"]
-        nr = self._dev[dev].get("n_real", 0)
+        nr = self._dev[dev].get("n_real_max", self._dev[dev].get("n_real", 0))
         M = self._dev[dev].get("M", 256)
         n, U, T, hist = np.zeros(N), np.zeros(N), np.zeros(max(nr, 1)), np.zeros(M)
         r = ScResult(_p(n), _p(U), _p(T), _p(hist), 0.0, 0, 0)
         rc = self.lib.negf_sc_end(self.h, dev, C.byref(r))
         if rc not in (OK, ENOTCONVERGED) or (check and rc):
             self._chk(rc)
+        nr = self._dev[dev]["n_real"] = self.grid_info(dev)["n_real"]
         return dict(status=rc, n=n, U=U, T=T[:nr], history=hist[:min(r.iterations, M)], I=r.I,
                     converged=bool(r.converged), iterations=r.iterations)
 

@@ -23,6 +23,13 @@ nanotube transistors, Sec. 3.1-3.3):
   started from the previous one's potential (the paper's sweep, Sec. 3.3-3.4).  The contact
   Fermi level sits 1 eV below midgap (the paper's Pd contacts, Sec. 3.1): mu = -1 eV with
   the leads at zero potential, so the contacts are metallic (p-type).
+* ``adaptive_lengths``  (17,0) mode-space channels of 224, 736 and 1760 rings (23.9, 78.4 and
+  187.4 nm, the lengths of Sec. 3.3), subband j = 6, drain ramp 0 -> -0.4 eV plus a 0.1 eV
+  barrier, V_DS = 0.4 V: quadrature error of the real-axis charge against the point count.
+* ``planar_array``      tubes side by side sharing contacts and gate (Sec. 3.4): five 96-ring
+  (10 nm) tubes at zero bias, and twenty 940-ring (100 nm) tubes at V_DS = 0.1 V, subbands
+  j = 6, 5, 2048 + 64 energies, contacts 1 eV below midgap; neighbouring tubes coupled with
+  a tenth of a tube's own gate coupling.
 """
 import numpy as np
 
@@ -137,3 +144,26 @@ def gate_sweep(N=96, n_points=31, v_lo=-1.0, v_hi=2.0, n_real=256, n_cont=64, mu
     return dict(name="gate_sweep", N=N, n_tube=N_TUBE, t=T_HOP, modes=(6, 5), kT=KT, eta=ETA,
                 mu=mu, V_DS=0.0, V_GS=np.linspace(v_lo, v_hi, n_points), n_real=n_real, n_cont=n_cont,
                 E_B=-3.0 * abs(T_HOP) - 1.0 - 0.5)
+
+
+def adaptive_lengths(lengths=(224, 736, 1760), V_DS=0.4):
+    """Channels for the semi-adaptive grid study (fixed potential, no self-consistency)."""
+    cases = []
+    for N in lengths:
+        U = ramp_barrier(N, drop=V_DS, height=0.1, width=N / 8.0)
+        cases.append(dict(N=N, U=U, U_S=0.0, U_D=-V_DS))
+    return dict(name="adaptive_lengths", n_tube=N_TUBE, t=T_HOP, modes=(6,), kT=KT, eta=ETA, mu_S=0.0,
+                mu_D=-V_DS, n_cont=64, E_B=-3.0 * abs(T_HOP) - 1.0 - V_DS, cases=cases)
+
+
+def planar_array(n_tubes=5, N=96, V_DS=0.0, V_GS=0.5, n_real=2048, n_cont=64, neighbour=0.1, mu=-1.0):
+    """Tubes of one planar array: coupling matrix K = kappa (I + neighbour * (nearest-neighbour
+    adjacency)), in units of kappa (the caller multiplies by the gate coupling), and the
+    seeded starting potentials (the linear drop between the contacts)."""
+    A = np.zeros((n_tubes, n_tubes))
+    for c in range(n_tubes - 1):
+        A[c, c + 1] = A[c + 1, c] = neighbour
+    U0 = np.tile(np.linspace(0.0, -V_DS, N), (n_tubes, 1))
+    return dict(name="planar_array", n_tubes=n_tubes, N=N, n_tube=N_TUBE, t=T_HOP, modes=(6, 5), kT=KT,
+                eta=ETA, mu_S=mu, mu_D=mu - V_DS, V_DS=V_DS, V_GS=V_GS, n_real=n_real, n_cont=n_cont,
+                E_B=-3.0 * abs(T_HOP) - 1.0 - V_DS + min(mu, 0.0), K_over_kappa=np.eye(n_tubes) + A, U0=U0)

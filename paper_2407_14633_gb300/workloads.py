@@ -279,3 +279,115 @@ def gate_sweep(w=None, tol=1e-8, M=64, warm=True):
     return {"V_GS": [float(v) for v in w["V_GS"]], "G_S": G, "iterations": iters, "converged": conv,
             "points_per_s": len(G) / wall, "seconds": wall,
             "ring_energy_mode_updates_per_s_wall": updates / wall}
+
+
+def adaptive_grid(budgets=(256, 512, 1024, 2048, 4096, 8192), ref_points=131072, ratios=(500.0, 1600.0, 50.0)):
+    """Semi-adaptive real-axis grid (Sec. 3.3) against one Gauss-Legendre rule at equal point
+    counts.  Per channel length: the real-axis charge of a 131072-point rule is the reference
+    (its own error estimated against half as many points); each budget is met by the plain rule
+    and by the semi-adaptive rule with densities in the paper's 500 : 1600 : 50 ratio and limits
+    E_s - 3 kT, E_s + kT around the peak E_s of the centre ring's integrand (located by two
+    refinements from a guess).  Reports the
+    norm-wise relative error of the real-axis charge, and the refinement cost next to one
+    evaluation of the same grid."""
+    w = synth.adaptive_lengths()
+    kT = w["kT"]
+    out = {}
+    for case in w["cases"]:
+        N = case["N"]
+        res = {"nm": round(N * 0.1065, 1), "plain": {}, "adaptive": {}}
+        with negf.Context() as ctx:
+            dev = ctx.device_create(N, block=1, rings_per_block=1, n_chains=1)
+            ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], list(w["modes"]), case["U_S"], case["U_D"])
+            ctx.set_potential(dev, case["U"])
+
+            def real_part(n_real):
+                ctx.set_grid_spec(dev, w["mu_S"], w["mu_D"], kT, w["eta"], w["E_B"], n_real, w["n_cont"])
+                return ctx.compute([dev])[0]["n_real"]
+            ref = real_part(ref_points)
+            res["reference_self_error"] = _rel(real_part(ref_points // 2), ref)
+            for nb in budgets:
+                res["plain"][nb] = _rel(real_part(nb), ref)
+            E_min = min(w["mu_S"], w["mu_D"]) - 14 * kT
+
+            def densities_for(nb, l1, l2):
+                # scale the 500 : 1600 : 50 densities so that the grid holds about nb points
+                lo, hi = 1e-6, 1e3
+                for _ in range(60):
+                    s = (lo * hi) ** 0.5
+                    g = negf.make_grid_adaptive(w["mu_S"], w["mu_D"], kT, w["eta"], w["E_B"], 0, l1, l2,
+                                                tuple(s * r for r in ratios))
+                    lo, hi = (s, hi) if g["E"].size < nb else (lo, s)
+                return tuple(hi * r for r in ratios)
+
+            # locate the peak: the first limits are a guess, two refinements move them onto it
+            l1, l2 = E_min + 0.3, E_min + 0.3 + 4 * kT
+            ctx.set_grid_adaptive(dev, w["mu_S"], w["mu_D"], kT, w["eta"], w["E_B"], w["n_cont"], l1, l2,
+                                  densities_for(4096, l1, l2))
+            ctx.refine_grid(dev)
+            t0 = time.perf_counter()
+            E_s = ctx.refine_grid(dev)
+            res["refine_ms"] = (time.perf_counter() - t0) * 1e3
+            t0 = time.perf_counter()
+            ctx.compute([dev])
+            res["evaluate_ms"] = (time.perf_counter() - t0) * 1e3
+            res["refine_points"] = ctx.grid_info(dev)["n_real"]
+            res["E_s"] = E_s
+            l1, l2 = E_s - 3 * kT, E_s + kT
+            for nb in budgets:
+                ctx.set_grid_adaptive(dev, w["mu_S"], w["mu_D"], kT, w["eta"], w["E_B"], w["n_cont"], l1, l2,
+                                      densities_for(nb, l1, l2))
+                nr = ctx.compute([dev])[0]["n_real"]
+                res["adaptive"][nb] = {"points": ctx.grid_info(dev)["n_real"], "error": _rel(nr, ref)}
+        out["N=%d" % N] = res
+    return out
+
+
+def multichannel(M=40, tol=1e-6):
+    """Planar arrays solved with one Broyden vector (negf_sc_solve_multi, Sec. 2.3).
+    Five 10 nm tubes at zero bias: iterations and the zero-bias conductance of each tube (the
+    outer tubes have one neighbour, the inner ones two).  Twenty 100 nm tubes at V_DS = 0.1 V:
+    time per self-consistent iteration of the coupled solve (all tubes in one launch) against
+    one tube solved alone, in ring-energy-mode updates per second."""
+    out = {}
+    kappa = negf.poisson_kappa()
+    w = synth.planar_array()
+    with negf.Context() as ctx:
+        devs = []
+        for _ in range(w["n_tubes"]):
+            d = ctx.device_create(w["N"], block=1, rings_per_block=1, n_chains=len(w["modes"]))
+            ctx.build_cnt_modespace(d, w["n_tube"], w["t"], list(w["modes"]), 0.0, -w["V_DS"])
+            ctx.set_grid_spec(d, w["mu_S"], w["mu_D"], w["kT"], w["eta"], w["E_B"], w["n_real"], w["n_cont"])
+            devs.append(d)
+        t0 = time.perf_counter()
+        r = ctx.sc_solve_multi(devs, w["V_DS"], w["V_GS"], w["U0"], kappa * w["K_over_kappa"], M=M, tol=tol,
+                               check=False)
+        wall = time.perf_counter() - t0
+        G = ctx.conductance(devs, w["mu_S"], w["kT"])
+        out["five_10nm"] = {"converged": r["converged"], "iterations": r["iterations"], "seconds": wall,
+                            "G_S": [float(x) for x in G], "U_mid": [float(u[w["N"] // 2]) for u in r["U"]]}
+    w = synth.planar_array(n_tubes=20, N=940, V_DS=0.1, V_GS=0.3)
+    lanes = len(w["modes"]) * (w["n_real"] + w["n_cont"])
+    with negf.Context() as ctx:
+        devs = []
+        for _ in range(w["n_tubes"]):
+            d = ctx.device_create(w["N"], block=1, rings_per_block=1, n_chains=len(w["modes"]))
+            ctx.build_cnt_modespace(d, w["n_tube"], w["t"], list(w["modes"]), 0.0, -w["V_DS"])
+            ctx.set_grid_spec(d, w["mu_S"], w["mu_D"], w["kT"], w["eta"], w["E_B"], w["n_real"], w["n_cont"])
+            devs.append(d)
+        ctx.sc_solve_multi(devs[:2], w["V_DS"], w["V_GS"], w["U0"][:2], kappa * w["K_over_kappa"][:2, :2], M=2,
+                           tol=tol, check=False)   # load the kernels
+        t0 = time.perf_counter()
+        r = ctx.sc_solve_multi(devs, w["V_DS"], w["V_GS"], w["U0"], kappa * w["K_over_kappa"], M=M, tol=tol,
+                               check=False)
+        wall = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        one = ctx.sc_solve(devs[0], w["V_DS"], w["V_GS"], w["U0"][0], kappa, M=M, tol=tol, check=False)
+        wall1 = time.perf_counter() - t0
+        out["twenty_100nm"] = {
+            "converged": r["converged"], "iterations": r["iterations"], "seconds": wall,
+            "ms_per_iteration": wall / r["iterations"] * 1e3,
+            "updates_per_s": w["n_tubes"] * w["N"] * lanes * r["iterations"] / wall,
+            "one_tube": {"iterations": one["iterations"], "ms_per_iteration": wall1 / one["iterations"] * 1e3,
+                         "updates_per_s": w["N"] * lanes * one["iterations"] / wall1}}
+    return out

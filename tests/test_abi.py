@@ -76,3 +76,15 @@ def test_product_path_never_imports_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+@pytest.mark.parametrize("limits,dens", [((-0.5, -0.4), (20.0, 80.0, 5.0)), ((-2.0, -0.7), (3.0, 7.5, 2.25)),
+                                         ((-0.2, 9.0), (1.0, 33.3, 0.7)), ((0.1, -0.3), (5.0, 5.0, 5.0))])
+def test_library_adaptive_grid_matches_oracle(lib, limits, dens):
+    from paper_2407_14633_gb300 import negf
+    r = negf.make_grid_adaptive(0.0, -0.4, 0.025, 1e-6, -11.0, 32, limits[0], limits[1], dens)
+    o = oq.adaptive_grid(0.0, -0.4, 0.025, limits[0], limits[1], dens, 32, -11.0, 1e-6)
+    assert r["E"].size == o["E"].size == sum(o["segments"])
+    for k in ("E", "w", "fS", "fD"):
+        assert np.max(np.abs(r[k] - o[k])) < 1e-13 * max(1.0, np.max(np.abs(o[k])))
+    assert np.max(np.abs(r["c"] - o["c"])) < 1e-13 * np.max(np.abs(o["c"]))
