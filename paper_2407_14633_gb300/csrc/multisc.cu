@@ -160,8 +160,6 @@ int negf_sc_solve_multi(negf_ctx* c, const int* devs, int C, const negf_bias* bi
       c->arena.release(*b);
     free_plan_bufs(c, bufs);
   };
-  std::vector<ChanDesc> chd(C);
-  for (int ci = 0; ci < C; ++ci) chd[ci] = ChanDesc{(double*)list[ci]->dU.p, (const double*)list[ci]->dn.p};
   if ((rc = upload(c, bnin, nin.data(), NT * 8)) || (rc = upload(c, bn0, n0.data(), NT * 8)) ||
       (rc = upload(c, bK, K.data(), (size_t)C * C * 8))) {
     cleanup();
@@ -181,13 +179,16 @@ int negf_sc_solve_multi(negf_ctx* c, const int* devs, int C, const negf_bias* bi
   cudaMemsetAsync(bhist.p, 0, M * 8, c->stream);
   cudaMemsetAsync(bm.p, 0, 4, c->stream);
   cudaMemsetAsync(bstate.p, 0, 4, c->stream);
-  if (cudaMemcpyAsync(bch.p, chd.data(), C * sizeof(ChanDesc), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
-    cleanup();
-    return set_err(c, NEGF_ECUDA, "upload failed");
-  }
   if ((rc = build_plan(c, list, nullptr, -1, plan, &bufs))) {
     cleanup();
     return rc;
+  }
+  // channel potentials and charges, taken once the plan has sized every output buffer
+  std::vector<ChanDesc> chd(C);
+  for (int ci = 0; ci < C; ++ci) chd[ci] = ChanDesc{(double*)list[ci]->dU.p, (const double*)list[ci]->dn.p};
+  if (cudaMemcpyAsync(bch.p, chd.data(), C * sizeof(ChanDesc), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    cleanup();
+    return set_err(c, NEGF_ECUDA, "upload failed");
   }
   ScDev sd;
   memset(&sd, 0, sizeof(sd));
