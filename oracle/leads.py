@@ -22,7 +22,9 @@ nanotubes, by a closed form (Sec. 2.2.2).  Both are written here:
   sum_d C[0, d] w^{jd}.  Each angular mode is then a dimerised chain with
   a1 = |lambda_j(T1)|^2, a2 = |lambda_j(T2)|^2 and Sigma = F diag(|lambda_j(tau)|^2 g_j) F^dagger.
 * ``lead_sigma_sancho``: decimation of the lead written as a uniform chain of two-ring
-  principal layers, fully general (no circulant assumption).
+  principal layers, fully general (no circulant assumption; the rings may carry on-site
+  blocks H0, H1 besides U, as a lead of another material or with a non-uniform potential
+  would).
 
 Gamma_l = i (Sigma_l - Sigma_l^dagger) (Sec. 2.2.1).
 
@@ -93,6 +95,8 @@ def lead_sigma_gamma_analytic(lead, eps):
     This is the same matrix as the site-basis difference, without its cancellation when
     every mode is closed (Gamma ~ eta, far below |Sigma|)."""
     eps = np.atleast_1d(np.asarray(eps, complex))
+    if lead.H0 is not None or lead.H1 is not None:
+        raise ValueError("leads with on-site blocks have no closed form here: use decimation")
     a1 = np.abs(circulant_eigenvalues(lead.T1)) ** 2
     a2 = np.abs(circulant_eigenvalues(lead.T2)) ** 2
     at = np.abs(circulant_eigenvalues(lead.tau)) ** 2
@@ -144,14 +148,16 @@ def surface_gf_sancho(eps, H00, H01, tol=1e-14, max_iter=400):
 def lead_sigma_sancho(lead, eps):
     """Sigma (E, m, m) of a lead by decimation over two-ring principal layers (s0, s1).
 
-    H00 = [[U, T1^dag], [T1, U]], H_{k,k+1} = [[0, 0], [T2^dag, 0]] (ring s1 of layer k to
-    ring s2 of layer k+1), g_{s0} = upper-left block of the layer surface function, and
-    Sigma = tau^dagger g_{s0} tau.
+    H00 = [[U + H0, T1^dag], [T1, U + H1]], H_{k,k+1} = [[0, 0], [T2^dag, 0]] (ring s1 of
+    layer k to ring s2 of layer k+1), g_{s0} = upper-left block of the layer surface
+    function, and Sigma = tau^dagger g_{s0} tau.
     """
     eps = np.atleast_1d(np.asarray(eps, complex))
     m = lead.m
     I = np.eye(m)
-    H00 = np.block([[lead.U * I, lead.T1.conj().T], [lead.T1, lead.U * I]])
+    h0 = lead.U * I + (0.0 if lead.H0 is None else np.asarray(lead.H0))
+    h1 = lead.U * I + (0.0 if lead.H1 is None else np.asarray(lead.H1))
+    H00 = np.block([[h0, lead.T1.conj().T], [lead.T1, h1]])
     Z = np.zeros((m, m))
     H01 = np.block([[Z, Z], [lead.T2.conj().T, Z]])
     gs = surface_gf_sancho(eps, H00, H01)[:, :m, :m]

@@ -44,6 +44,8 @@ class Lead:
     T2: np.ndarray      # (m, m) H_{s2,s1}
     tau: np.ndarray     # (m, m) H_{s0, boundary ring of the device}
     sites: np.ndarray   # (m,) site indices of the boundary ring inside its layer
+    H0: np.ndarray = None   # (m, m) on-site block of rings s0, s2, ... besides U (None: zero)
+    H1: np.ndarray = None   # (m, m) on-site block of rings s1, s3, ... besides U (None: zero)
 
     @property
     def m(self):

@@ -111,3 +111,67 @@ def test_mode_basis_gamma_is_the_definition():
     at = np.abs(ld.circulant_eigenvalues(lead.tau)) ** 2
     sig = at * ld.surface_gf_dimer(np.full(5, 0.1 + 1e-6j - lead.U), a1, a2)
     assert np.allclose(np.sort(np.linalg.eigvalsh(gm[0])), np.sort(-2 * sig.imag), rtol=1e-12, atol=1e-18)
+
+
+# ---- general (non-circulant) leads by decimation
+
+def random_general_lead(m, seed, onsite=True):
+    """A lead with random couplings and on-site blocks: no circulant structure, no closed form."""
+    rng = np.random.default_rng(seed)
+    T1 = -2.7 * np.eye(m) + 0.4 * (rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m)))
+    T2 = -2.2 * np.eye(m) + 0.4 * (rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m)))
+    tau = -2.5 * np.eye(m) + 0.3 * rng.normal(size=(m, m))
+    def herm():
+        X = rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m))
+        return 0.3 * (X + X.conj().T)
+    return mdl.Lead(0.1, T1, T2, tau, np.arange(m), H0=herm() if onsite else None, H1=herm() if onsite else None)
+
+
+def two_ring_map(lead, eps, g0):
+    """One step of the defining recursion of the two-ring lead: the surface function of ring
+    s0 from that of ring s2 (= s0 by periodicity):
+    g1 = (eps - U - H1 - T2^dag g0 T2)^{-1}, new g0 = (eps - U - H0 - T1^dag g1 T1)^{-1}."""
+    m = lead.m
+    I = np.eye(m)
+    h0 = lead.U * I + (0 if lead.H0 is None else lead.H0)
+    h1 = lead.U * I + (0 if lead.H1 is None else lead.H1)
+    g1 = np.linalg.inv(eps * I - h1 - lead.T2.conj().T @ g0 @ lead.T2)
+    return np.linalg.inv(eps * I - h0 - lead.T1.conj().T @ g1 @ lead.T1)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_general_lead_decimation_solves_the_defining_recursion(seed):
+    lead = random_general_lead(4, seed)
+    m = lead.m
+    I = np.eye(m)
+    h0 = lead.U * I + lead.H0
+    H00 = np.block([[h0, lead.T1.conj().T], [lead.T1, lead.U * I + lead.H1]])
+    H01 = np.block([[np.zeros((m, m)), np.zeros((m, m))], [lead.T2.conj().T, np.zeros((m, m))]])
+    for E in (-3.1, -0.4, 0.9, 4.2):
+        eps = E + 1e-4j
+        g0 = ld.surface_gf_sancho(np.array([eps]), H00, H01)[0, :m, :m]
+        assert np.max(np.abs(two_ring_map(lead, eps, g0) - g0)) < 1e-9 * np.max(np.abs(g0))
+        # retarded: the surface spectral function i (g - g^dagger) is positive semidefinite
+        assert np.min(np.linalg.eigvalsh(1j * (g0 - g0.conj().T))) > -1e-10 * np.max(np.abs(g0))
+        sig = ld.lead_sigma_sancho(lead, np.array([eps]))[0]
+        assert np.max(np.abs(sig - lead.tau.conj().T @ g0 @ lead.tau)) < 1e-12 * np.max(np.abs(sig))
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_general_lead_decimation_equals_plain_iteration(seed):
+    # with a broadening of 0.05 eV the plain fixed-point iteration of the recursion contracts to
+    # the retarded solution (an independent route to the same surface function)
+    lead = random_general_lead(3, seed)
+    for E in (-2.0, 0.3, 3.5):
+        eps = E + 0.05j
+        g = np.zeros((3, 3), complex)
+        for _ in range(20000):
+            g = two_ring_map(lead, eps, g)
+        sig_iter = lead.tau.conj().T @ g @ lead.tau
+        sig = ld.lead_sigma_sancho(lead, np.array([eps]))[0]
+        assert np.max(np.abs(sig - sig_iter)) < 1e-10 * np.max(np.abs(sig))
+
+
+def test_lead_with_onsite_blocks_has_no_closed_form_here():
+    with pytest.raises(ValueError):
+        ld.lead_sigma_analytic(random_general_lead(3, 7), np.array([0.3 + 1e-3j]))

@@ -270,3 +270,32 @@ def test_real_coupled_poisson_passes_its_pin():
 def test_coupled_poisson_pin_rejects(name, old, new):
     m = mutant("selfconsistent", old, new)
     assert coupled_poisson_gap(m) > 1e-6, name
+
+
+def general_lead_gap(leads_mod):
+    """Miss of the decimated surface function of a random non-circulant lead against the
+    defining two-ring recursion."""
+    from tests.test_oracle_leads import random_general_lead, two_ring_map
+    sg = leads_mod["lead_sigma_sancho"] if isinstance(leads_mod, dict) else leads_mod.lead_sigma_sancho
+    lead = random_general_lead(4, 2)
+    worst = 0.0
+    for E in (-0.4, 0.9):
+        eps = E + 1e-3j
+        sig = sg(lead, np.array([eps]))[0]
+        g0 = np.linalg.solve(lead.tau.conj().T, np.linalg.solve(lead.tau.T, sig.T).T)   # tau^-dag sig tau^-1
+        worst = max(worst, float(np.max(np.abs(two_ring_map(lead, eps, g0) - g0)) / np.max(np.abs(g0))))
+    return worst
+
+
+def test_real_general_lead_passes_its_pin():
+    assert general_lead_gap(ld) < 1e-8
+
+
+@pytest.mark.parametrize("name,old,new", [
+    ("decimation drops the c g a term", "h = h + agc + cga", "h = h + agc"),
+    ("on-site blocks of the two rings swapped", "H00 = np.block([[h0, lead.T1.conj().T], [lead.T1, h1]])",
+     "H00 = np.block([[h1, lead.T1.conj().T], [lead.T1, h0]])"),
+])
+def test_general_lead_pin_rejects(name, old, new):
+    m = mutant("leads", old, new)
+    assert general_lead_gap(m) > 1e-4, name
