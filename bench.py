@@ -349,7 +349,8 @@ def run_ours(args):
         runs = {"modespace_small": workloads.modespace_small, "batched_uneven": workloads.batched_uneven,
                 "mixed_precision": workloads.mixed_precision, "serving": workloads.serving_sweep,
                 "gate_sweep": lambda: {"warm": workloads.gate_sweep(), "cold": workloads.gate_sweep(warm=False)},
-                "adaptive_grid": workloads.adaptive_grid, "multichannel": workloads.multichannel}
+                "adaptive_grid": workloads.adaptive_grid, "multichannel": workloads.multichannel,
+                "general_leads": workloads.general_leads}
         pick = list(runs) if args.extras == "all" else args.extras.split(",")
         line["extras"] = {k: runs[k]() for k in pick}
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -425,7 +426,7 @@ def main():
     ap.add_argument("--extras", nargs="?", const="all", default=None,
                     help="also run the small, batched-uneven, mixed-precision, serving and gate-sweep workloads "
                          "(or a comma list of modespace_small, batched_uneven, mixed_precision, serving, "
-                         "gate_sweep, adaptive_grid, multichannel)")
+                         "gate_sweep, adaptive_grid, multichannel, general_leads)")
     ap.add_argument("--profile-small", action="store_true",
                     help="reduced case of the block sweep for ncu captures")
     ap.add_argument("--blk-warps", type=int, default=1,

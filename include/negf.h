@@ -141,6 +141,34 @@ typedef struct {
 } negf_lead;
 int negf_set_lead(negf_ctx* ctx, int dev, int chain, int side, const negf_lead* lead);
 
+/* A general (non-circulant) lead of one chain, for ring blocks wider than 2 (Eq. GR, Sec. 2.2.2:
+ * where no closed form applies the surface Green's function comes from Lopez Sancho-Rubio
+ * decimation).  The lead is a sequence of rings s0, s1, s2, ... moving away from the device,
+ * with m sites each (1 <= m <= 20), on-site blocks U_lead I + H0 on s0, s2, ... and
+ * U_lead I + H1 on s1, s3, ... (Hermitian; NULL = zero), couplings H_{s1,s0} = T1,
+ * H_{s2,s1} = T2, H_{s3,s2} = T1, ..., and device coupling tau = H_{s0, boundary ring}.  All
+ * blocks are full m x m complex matrices (row-major, interleaved), copied.  sites: the m
+ * distinct site indices of the boundary ring inside the first (source) or last (drain) layer.
+ * Every launch plan decimates the lead at each of its energies (two-ring principal layers,
+ * until the renormalised couplings fall below tol times the largest block entry, at most
+ * max_iter steps; 0 = defaults 1e-14 and 400), forms Sigma = tau^dagger g_{s0} tau and
+ * Gamma = i (Sigma - Sigma^dagger) and a pivoted Cholesky factor of Gamma for the sweep.
+ * Evaluations return NEGF_ENOTCONVERGED if a decimation hits max_iter.  negf_set_lead and
+ * the builders replace a general lead; negf_set_lead_potentials sets its U_lead. */
+typedef struct {
+  int m;
+  double U_lead;
+  const double* H0;
+  const double* H1;
+  const double* T1;
+  const double* T2;
+  const double* tau;
+  const int* sites;
+  int max_iter;
+  double tol;
+} negf_lead_general;
+int negf_set_lead_general(negf_ctx* ctx, int dev, int chain, int side, const negf_lead_general* lead);
+
 /* Lead potential energies only (U_S, U_D), keeping the couplings. */
 int negf_set_lead_potentials(negf_ctx* ctx, int dev, double U_S, double U_D);
 

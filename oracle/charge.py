@@ -100,8 +100,8 @@ def neutral_charge(device, n_cont, E_B, method="analytic", chunk=64):
     from .model import Device, Chain, Lead
     chains = []
     for ch in device.chains:
-        lS = Lead(0.0, ch.lead_S.T1, ch.lead_S.T2, ch.lead_S.tau, ch.lead_S.sites)
-        lD = Lead(0.0, ch.lead_D.T1, ch.lead_D.T2, ch.lead_D.tau, ch.lead_D.sites)
+        lS = Lead(0.0, ch.lead_S.T1, ch.lead_S.T2, ch.lead_S.tau, ch.lead_S.sites, ch.lead_S.H0, ch.lead_S.H1)
+        lD = Lead(0.0, ch.lead_D.T1, ch.lead_D.T2, ch.lead_D.tau, ch.lead_D.sites, ch.lead_D.H0, ch.lead_D.H1)
         chains.append(Chain(ch.Hdiag, ch.Hup, ch.site_ring, lS, lD, ch.g_b))
     r = negf_evaluate(Device(device.n_rings, chains), zero, grid, method, chunk)
     return r["n_cont"]

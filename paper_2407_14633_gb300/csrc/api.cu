@@ -89,7 +89,7 @@ void free_dev(Ctx* c, Dev* d) {
                     &ch.drs_val, &ch.dhsq, &ch.dHdiag_f, &ch.dcs_val_f, &ch.drs_val_f, &ch.dhsq_f})
       c->arena.release(*b);
     for (int s = 0; s < 2; ++s)
-      for (DBuf* b : {&ch.da1[s], &ch.da2[s], &ch.dat[s], &ch.dsites[s], &ch.dtw[s]})
+      for (DBuf* b : {&ch.da1[s], &ch.da2[s], &ch.dat[s], &ch.dsites[s], &ch.dtw[s], &ch.dgen[s]})
         c->arena.release(*b);
   }
   for (DBuf* b : {&d->dU, &d->dE, &d->dw, &d->dfS, &d->dfD, &d->dz, &d->dc, &d->dgb, &d->dn,
@@ -569,6 +569,7 @@ int negf_set_lead(negf_ctx* c, int dev, int chain, int side, const negf_lead* le
     if (lead->sites[s] < 0 || lead->sites[s] >= d->block)
       return set_err(c, NEGF_EINVAL, "lead site outside the boundary layer");
   HostLead& L = d->ch[chain].lead[side];
+  L.gen = false;
   L.m = lead->m;
   L.U = lead->U_lead;
   L.T1.assign(lead->T1, lead->T1 + 2 * L.m);
@@ -578,6 +579,63 @@ int negf_set_lead(negf_ctx* c, int dev, int chain, int side, const negf_lead* le
   cudaSetDevice(c->ordinal);
   int rc = upload_lead(c, d->ch[chain], side);
   if (rc) return rc;
+  L.set = true;
+  return NEGF_OK;
+}
+
+int negf_set_lead_general(negf_ctx* c, int dev, int chain, int side, const negf_lead_general* g) {
+  if (!c) return NEGF_EINVAL;
+  Dev* d = get_dev(c, dev);
+  if (!d) return set_err(c, NEGF_ENOTFOUND, "unknown device");
+  NEGF_NOT_IN_SESSION(c, d);
+  if (!g || chain < 0 || chain >= d->n_chains || (side != 0 && side != 1) || g->m < 1 || g->m > MAX_GEN_LEAD ||
+      g->m > d->block || !g->T1 || !g->T2 || !g->tau || !g->sites || !std::isfinite(g->U_lead) ||
+      g->max_iter < 0 || !(g->tol >= 0.0))
+    return set_err(c, NEGF_EINVAL, "bad general lead arguments");
+  if (d->block <= 2)
+    return set_err(c, NEGF_EINVAL, "general leads need ring blocks wider than 2 (single-site leads have a closed form)");
+  const int m = g->m;
+  for (int s = 0; s < m; ++s) {
+    if (g->sites[s] < 0 || g->sites[s] >= d->block) return set_err(c, NEGF_EINVAL, "lead site outside the boundary layer");
+    for (int t = 0; t < s; ++t)
+      if (g->sites[t] == g->sites[s]) return set_err(c, NEGF_EINVAL, "lead site listed twice");
+  }
+  const size_t mm2 = (size_t)2 * m * m;
+  std::vector<double> mats(5 * mm2, 0.0);
+  const double* src[5] = {g->H0, g->H1, g->T1, g->T2, g->tau};
+  for (int k = 0; k < 5; ++k)
+    if (src[k]) std::copy(src[k], src[k] + mm2, mats.begin() + k * mm2);
+  for (double v : mats)
+    if (!std::isfinite(v)) return set_err(c, NEGF_EINVAL, "non-finite general lead entry");
+  // the on-site blocks must be Hermitian
+  for (int k = 0; k < 2; ++k)
+    for (int r = 0; r < m; ++r)
+      for (int q = 0; q < m; ++q) {
+        const double* a = mats.data() + k * mm2 + 2 * (r * m + q);
+        const double* b = mats.data() + k * mm2 + 2 * (q * m + r);
+        if (std::fabs(a[0] - b[0]) > 1e-12 * (1.0 + std::fabs(a[0])) || std::fabs(a[1] + b[1]) > 1e-12 * (1.0 + std::fabs(a[1])))
+          return set_err(c, NEGF_EINVAL, "on-site block of a general lead is not Hermitian");
+      }
+  cudaSetDevice(c->ordinal);
+  ChainData& ch = d->ch[chain];
+  int rc = upload(c, ch.dgen[side], mats.data(), mats.size() * 8);
+  if (rc) return rc;
+  std::vector<int> sites(g->sites, g->sites + m);
+  if ((rc = upload(c, ch.dsites[side], sites.data(), sites.size() * sizeof(int)))) return rc;
+  HostLead& L = ch.lead[side];
+  L.m = m;
+  L.U = g->U_lead;
+  L.gen = true;
+  L.gmats = mats;
+  L.max_iter = g->max_iter ? g->max_iter : 400;
+  L.tol = g->tol > 0.0 ? g->tol : 1e-14;
+  L.sites = sites;
+  // no closed-form band edges (the mixed path's edge windows skip this lead) and no first rows
+  L.a1.clear();
+  L.a2.clear();
+  L.T1.assign(2 * m, 0.0);
+  L.T2.assign(2 * m, 0.0);
+  L.tau.assign(2 * m, 0.0);
   L.set = true;
   return NEGF_OK;
 }

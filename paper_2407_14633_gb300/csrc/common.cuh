@@ -25,16 +25,19 @@ template <typename T>
 __host__ __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.re + b.re, a.im + b.im); }
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+// Every product that feeds a sum is an explicit fused multiply-add, so the compiler has no
+// contraction left to choose and each template instantiation (CTA width, element type)
+// evaluates it in the same bits.
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
-  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+  return mk(fma(a.re, b.re, -(a.im * b.im)), fma(a.re, b.im, a.im * b.re));
 }
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> scale(cx<T> a, T s) { return mk(a.re * s, a.im * s); }
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> conjg(cx<T> a) { return mk(a.re, -a.im); }
 template <typename T>
-__host__ __device__ __forceinline__ T abs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
+__host__ __device__ __forceinline__ T abs2(cx<T> a) { return fma(a.re, a.re, a.im * a.im); }
 // acc + a * b with fused multiply-adds (4 FMA)
 template <typename T>
 __host__ __device__ __forceinline__ cx<T> cmac(cx<T> acc, cx<T> a, cx<T> b) {
@@ -91,7 +94,31 @@ struct LeadView {
   const double* at; // m
   const int* sites; // m site indices inside the boundary layer
   const double* tw; // 2m: cos, sin of 2 pi k / m (k = 0..m-1), interleaved
+  // general (non-circulant) lead: Sigma and a factor L of Gamma = L L^dagger at every energy
+  // of the view (real-axis energies first, then contour nodes), m x m each, from the
+  // decimation kernel of the launch plan
+  int gen;
+  const cd* gsig;
+  const cd* gfac;
 };
+
+// Decimation job of one general lead over every energy of one device view (lead_general.cu).
+struct GenLeadJob {
+  const cd* mats;   // H0, H1, T1, T2, tau: 5 m x m blocks (lead rings s0, s1; H_{s1,s0}, H_{s2,s1}, H_{s0,device})
+  int m;
+  double U;         // lead potential energy (added on both rings)
+  int n_real, n_cont;
+  const double* E;  // real-axis energies (E + i eta)
+  double eta;
+  const cd* z;      // contour nodes
+  cd* sig;          // out: (n_real + n_cont) x m x m
+  cd* fac;          // out: (n_real + n_cont) x m x m
+  int max_iter;
+  double tol;
+};
+constexpr int MAX_GEN_LEAD = 20;   // widest general lead ring (its two-ring layers are 2m wide)
+int launch_lead_general(const GenLeadJob* jobs, int n_jobs, int max_energies, int m_max, int* status,
+                        cudaStream_t s);
 
 // One chain of one device.
 struct ChainView {

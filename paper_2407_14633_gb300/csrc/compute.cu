@@ -84,7 +84,8 @@ DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
     for (int s2 = 0; s2 < 2; ++s2)
       for (const std::vector<double>* f : {&ch.lead[s2].T1, &ch.lead[s2].T2, &ch.lead[s2].tau})
         for (size_t i = 1; i < f->size(); i += 2) lead_real = lead_real && (*f)[i] == 0.0;
-    cv.sym = (ch.h_sym && lead_real && !c->opts.general_update) ? 1 : 0;
+    // (general leads take the general update: their Sigma comes from decimation)
+    cv.sym = (ch.h_sym && lead_real && !ch.lead[0].gen && !ch.lead[1].gen && !c->opts.general_update) ? 1 : 0;
     for (int s = 0; s < 2; ++s) {
       LeadView& lv = cv.lead[s];
       lv.m = ch.lead[s].m;
@@ -94,6 +95,9 @@ DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
       lv.at = (const double*)ch.dat[s].p;
       lv.sites = (const int*)ch.dsites[s].p;
       lv.tw = (const double*)ch.dtw[s].p;
+      lv.gen = ch.lead[s].gen ? 1 : 0;   // per-energy blocks are attached by build_plan
+      lv.gsig = nullptr;
+      lv.gfac = nullptr;
     }
   }
   return v;
@@ -114,7 +118,7 @@ int check_ready(Ctx* c, Dev* d) {
 // reset, sweeps, second stage), so it can be captured in a CUDA graph and replayed.
 void free_plan_bufs(Ctx* c, PlanBufs& b) {
   for (DBuf* x : {&b.views, &b.items, &b.order, &b.counter, &b.partial, &b.tpart, &b.stage, &b.reduce, &b.status,
-                  &b.resid, &b.order2, &b.growth, &b.prep, &b.hu})
+                  &b.resid, &b.order2, &b.growth, &b.prep, &b.hu, &b.gen, &b.genjobs, &b.genstat})
     c->arena.release(*x);
 }
 
@@ -559,6 +563,51 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
   }
   P.n_prep = n_prep;
   P.prep_L = prep_L;
+  // general leads: Sigma and the factor of Gamma at every energy of each view, by decimation
+  // (lead_general.cu), computed once per plan: the plan's energies and lead potentials are fixed
+  std::vector<GenLeadJob> jobs;
+  {
+    long long gen_elems = 0;
+    for (int di = 0; di < nd; ++di)
+      for (int ch = 0; ch < devs[di]->n_chains; ++ch)
+        for (int sd = 0; sd < 2; ++sd)
+          if (devs[di]->ch[ch].lead[sd].gen) {
+            const int m = devs[di]->ch[ch].lead[sd].m;
+            gen_elems += 2LL * (P.views[di].n_real + P.views[di].n_cont) * m * m;
+          }
+    if (gen_elems > 0) {
+      if (!ensure(c, B.gen, sizeof(cd) * gen_elems) || !ensure(c, B.genstat, sizeof(int))) return NEGF_ENOMEM;
+      cd* base = (cd*)B.gen.p;
+      long long off = 0;
+      for (int di = 0; di < nd; ++di) {
+        DeviceView& v = P.views[di];
+        for (int ch = 0; ch < devs[di]->n_chains; ++ch)
+          for (int sd = 0; sd < 2; ++sd) {
+            const HostLead& HL = devs[di]->ch[ch].lead[sd];
+            if (!HL.gen) continue;
+            const long long ne = (long long)(v.n_real + v.n_cont) * HL.m * HL.m;
+            GenLeadJob j;
+            j.mats = (const cd*)devs[di]->ch[ch].dgen[sd].p;
+            j.m = HL.m;
+            j.U = v.ch[ch].lead[sd].U;   // zero under the neutral-charge override
+            j.n_real = v.n_real;
+            j.n_cont = v.n_cont;
+            j.E = v.E;
+            j.eta = v.eta;
+            j.z = v.z;
+            j.sig = base + off;
+            j.fac = base + off + ne;
+            j.max_iter = HL.max_iter;
+            j.tol = HL.tol;
+            v.ch[ch].lead[sd].gsig = j.sig;
+            v.ch[ch].lead[sd].gfac = j.fac;
+            jobs.push_back(j);
+            off += 2 * ne;
+          }
+      }
+      if (!ensure(c, B.genjobs, sizeof(GenLeadJob) * jobs.size())) return NEGF_ENOMEM;
+    }
+  }
   // synchronous uploads: the host vectors die with this call
   if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
       (n_prep && cudaMemcpy(B.prep.p, prep.data(), sizeof(PrepDesc) * n_prep, cudaMemcpyHostToDevice)) ||
@@ -567,6 +616,23 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       cudaMemcpy(B.order.p, order_all.data(), sizeof(int) * n_items, cudaMemcpyHostToDevice) ||
       cudaMemcpy(B.reduce.p, rd.data(), sizeof(ReduceDev) * nd, cudaMemcpyHostToDevice))
     return set_err(c, NEGF_ECUDA, "upload of the launch plan failed");
+  if (!jobs.empty()) {
+    int max_e = 1, m_max = 1;
+    for (const GenLeadJob& j : jobs) {
+      max_e = std::max(max_e, j.n_real + j.n_cont);
+      m_max = std::max(m_max, j.m);
+    }
+    int nonconv = 0;
+    if (cudaMemcpy(B.genjobs.p, jobs.data(), sizeof(GenLeadJob) * jobs.size(), cudaMemcpyHostToDevice) ||
+        cudaMemsetAsync(B.genstat.p, 0, sizeof(int), c->stream) ||
+        launch_lead_general((const GenLeadJob*)B.genjobs.p, (int)jobs.size(), max_e, m_max, (int*)B.genstat.p,
+                            c->stream) ||
+        cudaMemcpyAsync(&nonconv, B.genstat.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream) ||
+        cudaStreamSynchronize(c->stream))
+      return set_err(c, NEGF_ECUDA, "lead decimation failed");
+    ++c->launches;
+    if (nonconv) return set_err(c, NEGF_ENOTCONVERGED, "lead decimation did not converge at some energies");
+  }
   for (int g = 0; g < NGROUPS; ++g)
     if (tune_g[g]) {
       int rc = tune_width(c, P, g);

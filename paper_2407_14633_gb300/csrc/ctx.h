@@ -38,6 +38,12 @@ struct HostLead {
   std::vector<double> T1, T2, tau;  // first rows, 2m each
   std::vector<int> sites;
   bool set = false;
+  // general lead (negf_set_lead_general): full m x m blocks H0, H1, T1, T2, tau (interleaved
+  // complex, 2 m^2 doubles each), decimation limits
+  bool gen = false;
+  std::vector<double> gmats;   // H0 | H1 | T1 | T2 | tau
+  int max_iter = 400;
+  double tol = 1e-14;
 };
 
 struct ChainData {
@@ -51,6 +57,7 @@ struct ChainData {
   DBuf dHdiag_f, dcs_val_f, drs_val_f, dhsq_f;   // FP32 copies for the complex64 sweeps
   bool diag_real = false;                        // Im H_ll = 0 everywhere
   DBuf da1[2], da2[2], dat[2], dsites[2], dtw[2];
+  DBuf dgen[2];   // general leads: the five m x m blocks on the device
   int kmax = 0;
 };
 
@@ -60,6 +67,7 @@ struct ChainData {
 struct PlanBufs {
   DBuf views, items, order, counter, partial, tpart, stage, reduce, status, resid, order2, growth;
   DBuf prep, hu;   // layer diagonals of the 1 x 1 chains (descriptors, values)
+  DBuf gen, genjobs, genstat;   // general leads: per-energy Sigma and Gamma factors, jobs, status
 };
 
 struct ScSession;

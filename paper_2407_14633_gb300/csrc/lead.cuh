@@ -26,19 +26,20 @@ __device__ __forceinline__ cd csqrt_principal(cd z) {
 }
 
 __device__ __forceinline__ cd cdiv(cd a, cd b) {
-  double s = 1.0 / (b.re * b.re + b.im * b.im);
-  return mk((a.re * b.re + a.im * b.im) * s, (a.im * b.re - a.re * b.im) * s);
+  double s = 1.0 / fma(b.re, b.re, b.im * b.im);
+  return mk(fma(a.re, b.re, a.im * b.im) * s, fma(a.im, b.re, -(a.re * b.im)) * s);
 }
 
 // surface Green's function of the dimerised chain at complex energy eps
 __device__ __forceinline__ cd surface_gf(cd eps, double a1, double a2) {
   if (a2 == 0.0) {
-    cd den = mk(eps.re * eps.re - eps.im * eps.im - a1, 2.0 * eps.re * eps.im);
+    cd den = mk(fma(eps.re, eps.re, -(eps.im * eps.im)) - a1, 2.0 * eps.re * eps.im);
     return cdiv(eps, den);
   }
   cd e2 = eps * eps;
   cd B = mk(e2.re - a1 + a2, e2.im);
-  cd disc = B * B - scale(e2, 4.0 * a2);
+  const cd BB = B * B;
+  cd disc = mk(fma(-e2.re, 4.0 * a2, BB.re), fma(-e2.im, 4.0 * a2, BB.im));
   cd s = csqrt_principal(disc);
   cd qp = B + s, qm = B - s;
   cd q = (abs2(qp) >= abs2(qm)) ? qp : qm;

@@ -4,7 +4,8 @@
 //
 // The algorithm is the left-connected recursion (Alg. 2 reading) with the lead columns
 // propagated as factors of the broadening matrices, Gamma_l = L_l L_l^dagger with
-// L_l = F diag(sqrt(gamma_j)) from the circulant lead (F the ring Fourier basis):
+// L_l = F diag(sqrt(gamma_j)) from a circulant lead (F the ring Fourier basis), or the
+// pivoted Cholesky factor that the launch plan computes per energy for a general lead:
 //   forward   X = H_{l,l-1} gL_{l-1},  gL_l = (alpha_l - X H_{l-1,l})^{-1},
 //             R_l = X R_{l-1} (R_0 = L_S)                 [R_l = G_{l,l}^{-1} G_{l,0} L_S]
 //   backward  Z = gL_l H_{l,l+1},  G_ll = gL_l + Z G_{l+1,l+1} (H_{l+1,l} gL_l),
@@ -513,11 +514,12 @@ __host__ __device__ size_t sweep_blk_smem_bytes_t(int b, int m, int esize, int w
 }
 
 // alpha_l - Sub (Sub may be null): eps I - H_ll - U_ring - Sigma_S (l = 0) - Sigma_D (l = L-1),
-// assembled in FP64 and rounded to T
+// assembled in FP64 and rounded to T.  A circulant lead's Sigma comes from its first row
+// (sigS / sigD); a general lead's from the plan's per-energy blocks (energy index eidx).
 template <typename T, int NW>
 __device__ __forceinline__ void alpha_minus(cx<T>* out, const cx<T>* Sub, int l, int L, int b, int rpb, int spr,
                                             cd eps, const DeviceView& D, const ChainView& C, const cd* sigS,
-                                            const cd* sigD, int tid) {
+                                            const cd* sigD, int eidx, int tid) {
   constexpr int NT = 32 * NW;
   const cx<T>* hd = hdiag_t<T>(C) + (long long)l * b * b;
   const int nn = b * b;
@@ -532,10 +534,11 @@ __device__ __forceinline__ void alpha_minus(cx<T>* out, const cx<T>* Sub, int l,
     const LeadView& Lv = C.lead[side];
     const cd* row = side ? sigD : sigS;
     const int m = Lv.m;
+    const cd* gsig = Lv.gen ? Lv.gsig + (long long)eidx * m * m : nullptr;
     for (int o = tid; o < m * m; o += NT) {
       const int s = o / m, t = o - s * m;
       const int q = Lv.sites[s] * b + Lv.sites[t];
-      out[q] = out[q] - tc<T>(row[((s - t) % m + m) % m]);
+      out[q] = out[q] - tc<T>(gsig ? gsig[o] : row[((s - t) % m + m) % m]);
     }
     csync<NW>();
   }
@@ -596,6 +599,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
     cd eps;
     double wS = 0.0, wD = 0.0;
     cd kap = mk(0.0, 0.0);
+    const int eidx = real ? k : D.n_real + k;   // energy index of the view (general leads)
     if (real) {
       eps = mk(D.E[k], D.eta);
       wS = g * D.w[k] * D.fS[k] * (0.5 / 3.14159265358979323846);
@@ -610,6 +614,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
     //      (a thread holds at most two modes: m <= MAX_LEAD <= 2 * NT)
     for (int side = 0; side < 2; ++side) {
       const LeadView& Lv = C.lead[side];
+      if (Lv.gen) continue;   // general lead: Sigma and its Gamma factor come from the plan
       cd* row = side ? sigD : sigS;
       double* sq = side ? sqD : sqS;
       const int m = Lv.m;
@@ -662,19 +667,21 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
         if constexpr (CMP) {
           if (real) store_r<T, NT>(Rn, mS, rt, b, mS, tid);   // read before the next barrier (binv)
         }
-        alpha_minus<T, NW>(A, A, l, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);  // alpha_l - y_l
+        alpha_minus<T, NW>(A, A, l, L, b, rpb, spr, eps, D, C, sigS, sigD, eidx, tid);  // alpha_l - y_l
       } else {
         if (real) {
           // R_0 = L_S: rows at the lead sites, L_S[site_s][j] = w^{j s} sqrt(gamma_j / m)
+          // (circulant lead) or the plan's factor of Gamma_S (general lead)
           for (int o = tid; o < b * mS; o += NT) Rn[o] = cz<T>();
           csync<NW>();
+          const cd* fS = LS.gen ? LS.gfac + (long long)eidx * mS * mS : nullptr;
           for (int o = tid; o < mS * mS; o += NT) {
             const int s = o / mS, j = o - s * mS;
             const int e = (j * s) % mS;
-            Rn[LS.sites[s] * mS + j] = tc<T>(scale(mk(LS.tw[2 * e], LS.tw[2 * e + 1]), sqS[j]));
+            Rn[LS.sites[s] * mS + j] = tc<T>(fS ? fS[o] : scale(mk(LS.tw[2 * e], LS.tw[2 * e + 1]), sqS[j]));
           }
         }
-        alpha_minus<T, NW>(A, nullptr, 0, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);
+        alpha_minus<T, NW>(A, nullptr, 0, L, b, rpb, spr, eps, D, C, sigS, sigD, eidx, tid);
       }
       binv<T, NW>(A, b, col, perm, redf, redi, tid);
       if (!TWO && C.sym)   // largest |gL_l diagonal|^2 seen by this thread (symmetric-update gate)
@@ -734,20 +741,27 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
     }
     if (real) {
       // K_{L-1} = G_{L-1,L-1} L_D: K[r][j] = sum_s G[r][site_s] w^{j s} sqrt(gamma_j/m)
+      // (circulant lead) or sum_s G[r][site_s] L_D[s][j] (general lead)
+      const cd* fD = LD.gen ? LD.gfac + (long long)eidx * mD * mD : nullptr;
       for (int o = tid; o < b * mD; o += NT) {
         const int r = o / mD, j = o - r * mD;
         cx<T> acc = cz<T>();
-        for (int s = 0; s < mD; ++s) {
-          const int e = (j * s) % mD;
-          acc = cmac(acc, G[r * b + LD.sites[s]], tc<T>(mk(LD.tw[2 * e], LD.tw[2 * e + 1])));
+        if (fD) {
+          for (int s = 0; s < mD; ++s) acc = cmac(acc, G[r * b + LD.sites[s]], tc<T>(fD[s * mD + j]));
+          K[o] = acc;
+        } else {
+          for (int s = 0; s < mD; ++s) {
+            const int e = (j * s) % mD;
+            acc = cmac(acc, G[r * b + LD.sites[s]], tc<T>(mk(LD.tw[2 * e], LD.tw[2 * e + 1])));
+          }
+          K[o] = scale(acc, (T)sqD[j]);
         }
-        K[o] = scale(acc, (T)sqD[j]);
       }
       csync<NW>();
     }
     if (TWO && L > 1) {
       // gR_{L-1} = alpha_{L-1}^{-1} (into Wm), gL_{L-2} into GlB
-      alpha_minus<T, NW>(Wm, nullptr, L - 1, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);
+      alpha_minus<T, NW>(Wm, nullptr, L - 1, L, b, rpb, spr, eps, D, C, sigS, sigD, eidx, tid);
       binv<T, NW>(Wm, b, col, perm, redf, redi, tid);
       const cx<T>* sg = reinterpret_cast<const cx<T>*>(stage + (long long)(L - 2) * lstride);
       for (int o = tid; o < nn; o += NT) GlB[o] = sg[o];
@@ -830,7 +844,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
           if (real) bgemm<T, NT>(Kn, mD, Wk, b, K, mD, b, b, mD, nullptr, 0, tid);   // K_l = gL_l H K_{l+1}
           times_hdn<T, NT>(G, W1, b, b, rcnt, ridx, rval, kmax, tid);                  // x_l (into G)
           csync<NW>();
-          alpha_minus<T, NW>(Gr, G, l, L, b, rpb, spr, eps, D, C, sigS, sigD, tid);  // alpha_l - x_l
+          alpha_minus<T, NW>(Gr, G, l, L, b, rpb, spr, eps, D, C, sigS, sigD, eidx, tid);  // alpha_l - x_l
           if (l > 0) {
             const int* pcnt = C.cs_cnt + (long long)(l - 1) * b;
             const int* pidx = C.cs_idx + (long long)(l - 1) * b * kmax;
@@ -868,17 +882,16 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
             T as = T(0), ad = T(0);
             for (int j = 0; j < mS; ++j) as = fma(Pm[r * mS + j].im, Pm[r * mS + j].im, fma(Pm[r * mS + j].re, Pm[r * mS + j].re, as));
             for (int j = 0; j < mD; ++j) ad = fma(K[r * mD + j].im, K[r * mD + j].im, fma(K[r * mD + j].re, K[r * mD + j].re, ad));
-            vr[r / spr] += wS * (double)as + wD * (double)ad;
+            vr[r / spr] = fma(wS, (double)as, fma(wD, (double)ad, vr[r / spr]));
             if (a.resid) {
-              const T gim2 = T(2) * G[r * b + r].im;
-              rnum = fmax(rnum, as + ad + gim2);
-              rden = fmax(rden, fabs(gim2));
+              rnum = fmax(rnum, fma(T(2), G[r * b + r].im, as + ad));
+              rden = fmax(rden, fabs(T(2) * G[r * b + r].im));
             }
           }
       } else if (tid < 32) {
         for (int r = tid; r < b; r += 32) {
           const cx<T> gd = G[r * b + r];
-          vr[r / spr] += kap.re * (double)gd.im + kap.im * (double)gd.re;
+          vr[r / spr] = fma(kap.re, (double)gd.im, fma(kap.im, (double)gd.re, vr[r / spr]));
         }
       }
       if (tid < 32)
@@ -892,15 +905,21 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 9 : (NW == 2 ? 6 : 3)) swee
       // T = || L_S^dag K_0 ||_F^2, (L_S^dag K_0)[i][j] = sum_s conj(L_S[site_s][i]) K_0[site_s][j]
       // (warp 0, fixed lane mapping)
       double tv = 0.0;
+      const cd* fS = LS.gen ? LS.gfac + (long long)eidx * mS * mS : nullptr;
       if (tid < 32)
         for (int o = tid; o < mS * mD; o += 32) {
           const int i = o / mD, j = o - i * mD;
           cx<T> acc = cz<T>();
-          for (int s = 0; s < mS; ++s) {
-            const int e = (i * s) % mS;
-            acc = cmac_cj(acc, tc<T>(mk(LS.tw[2 * e], LS.tw[2 * e + 1])), K[LS.sites[s] * mD + j]);
+          if (fS) {
+            for (int s = 0; s < mS; ++s) acc = cmac_cj(acc, tc<T>(fS[s * mS + i]), K[LS.sites[s] * mD + j]);
+            tv += (double)abs2(acc);
+          } else {
+            for (int s = 0; s < mS; ++s) {
+              const int e = (i * s) % mS;
+              acc = cmac_cj(acc, tc<T>(mk(LS.tw[2 * e], LS.tw[2 * e + 1])), K[LS.sites[s] * mD + j]);
+            }
+            tv = fma((double)abs2(acc), sqS[i] * sqS[i], tv);
           }
-          tv += (double)abs2(acc) * sqS[i] * sqS[i];
         }
       const double Tval = tid < 32 ? wsum(tv) : 0.0;
       if (tid == 0) a.Tpart[W.tout] = Tval;

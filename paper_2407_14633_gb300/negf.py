@@ -33,6 +33,11 @@ class Lead(C.Structure):
                 ("sites", _ip)]
 
 
+class LeadGeneral(C.Structure):
+    _fields_ = [("m", C.c_int), ("U_lead", C.c_double), ("H0", _dp), ("H1", _dp), ("T1", _dp), ("T2", _dp),
+                ("tau", _dp), ("sites", _ip), ("max_iter", C.c_int), ("tol", C.c_double)]
+
+
 class Grid(C.Structure):
     _fields_ = [("n_real", C.c_int), ("E", _dp), ("w", _dp), ("fS", _dp), ("fD", _dp), ("eta", C.c_double),
                 ("n_cont", C.c_int), ("z", _dp), ("c", _dp)]
@@ -92,6 +97,7 @@ _PROTOS = {
     "negf_set_hamiltonian": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _dp, _dp, C.c_double]),
     "negf_set_lead": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(Lead)]),
     "negf_set_lead_potentials": (C.c_int, [C.c_void_p, C.c_int, C.c_double, C.c_double]),
+    "negf_set_lead_general": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, C.POINTER(LeadGeneral)]),
     "negf_build_cnt_modespace": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, _ip, C.c_double, C.c_double]),
     "negf_build_cnt_realspace": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double]),
     "negf_set_potential": (C.c_int, [C.c_void_p, C.c_int, _dp]),
@@ -297,6 +303,14 @@ class Context:
         st = np.ascontiguousarray(sites, dtype=np.int32)
         ld = Lead(m, U_lead, _p(t1), _p(t2), _p(tau), _pi(st))
         self._chk(self.lib.negf_set_lead(self.h, dev, chain, side, C.byref(ld)))
+
+    def set_lead_general(self, dev, chain, side, U_lead, T1, T2, tau, sites, H0=None, H1=None, max_iter=0, tol=0.0):
+        """negf_set_lead_general: a non-circulant lead (m x m complex blocks), decimated per energy."""
+        m = len(sites)
+        mats = [None if x is None else _cplx(np.asarray(x).reshape(-1), m * m) for x in (H0, H1, T1, T2, tau)]
+        st = np.ascontiguousarray(sites, dtype=np.int32)
+        ld = LeadGeneral(m, U_lead, *[_p(x) for x in mats], _pi(st), max_iter, tol)
+        self._chk(self.lib.negf_set_lead_general(self.h, dev, chain, side, C.byref(ld)))
 
     def set_lead_potentials(self, dev, U_S, U_D):
         self._chk(self.lib.negf_set_lead_potentials(self.h, dev, U_S, U_D))

@@ -167,3 +167,20 @@ def planar_array(n_tubes=5, N=96, V_DS=0.0, V_GS=0.5, n_real=2048, n_cont=64, ne
     return dict(name="planar_array", n_tubes=n_tubes, N=N, n_tube=N_TUBE, t=T_HOP, modes=(6, 5), kT=KT,
                 eta=ETA, mu_S=mu, mu_D=mu - V_DS, V_DS=V_DS, V_GS=V_GS, n_real=n_real, n_cont=n_cont,
                 E_B=-3.0 * abs(T_HOP) - 1.0 - V_DS + min(mu, 0.0), K_over_kappa=np.eye(n_tubes) + A, U0=U0)
+
+
+def general_lead(m, seed, t=T_HOP, onsite=0.3, disorder=0.4):
+    """A lead without circulant structure: couplings T1, T2, tau near t I with seeded complex
+    (T1, T2) or real (tau) perturbations, and seeded Hermitian on-site blocks H0, H1 (interleaved
+    m x m complex arrays, as the C ABI takes them)."""
+    rng = np.random.default_rng(seed)
+    def pert(cplx):
+        X = rng.normal(size=(m, m)) + (1j * rng.normal(size=(m, m)) if cplx else 0.0)
+        return disorder * X
+    def herm():
+        X = rng.normal(size=(m, m)) + 1j * rng.normal(size=(m, m))
+        return onsite * 0.5 * (X + X.conj().T)
+    T1 = t * np.eye(m) + pert(True)
+    T2 = 0.8 * t * np.eye(m) + pert(True)
+    tau = 0.9 * t * np.eye(m) + pert(False)
+    return dict(T1=T1, T2=T2, tau=tau.astype(complex), H0=herm(), H1=herm())

@@ -391,3 +391,38 @@ def multichannel(M=40, tol=1e-6):
             "one_tube": {"iterations": one["iterations"], "ms_per_iteration": wall1 / one["iterations"] * 1e3,
                          "updates_per_s": w["N"] * lanes * one["iterations"] / wall1}}
     return out
+
+
+def general_leads(reps=3):
+    """General (non-circulant) leads on the 17 x 17 real-space workload (N = 512, 2048 + 128
+    energies): one evaluation with seeded non-circulant leads (synth.general_lead), decimated
+    per energy when the plan is built, against the same tube with its circulant leads (closed
+    form per angular mode).  Wall time per negf_compute (plan, decimation, sweep, second stage)
+    and the event-timed sweep alone."""
+    w = synth.realspace_17()
+    out = {}
+    for kind in ("circulant", "general"):
+        with negf.Context() as ctx:
+            dev = ctx.device_create(w["N"], block=17, rings_per_block=1, n_chains=1)
+            ctx.build_cnt_realspace(dev, 17, w["t"], w["U_S"], w["U_D"])
+            if kind == "general":
+                for side, (seed, U_l) in enumerate(((41, w["U_S"]), (42, w["U_D"]))):
+                    ld = synth.general_lead(17, seed)
+                    ctx.set_lead_general(dev, 0, side, U_l, ld["T1"], ld["T2"], ld["tau"], list(range(17)),
+                                         H0=ld["H0"], H1=ld["H1"])
+            ctx.set_potential(dev, w["U"])
+            ctx.set_grid_spec(dev, w["mu_S"], w["mu_D"], w["kT"], w["eta"], w["E_B"], w["n_real"], w["n_cont"])
+            ctx.compute([dev])   # tuning and kernel loads
+            ctx.profile(True)
+            ctx.kernel_time()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                r = ctx.compute([dev])[0]
+            wall = (time.perf_counter() - t0) / reps
+            ms, k = ctx.kernel_time()
+        out[kind] = {"compute_ms": wall * 1e3, "sweep_ms": ms / max(k, 1), "I": r["I"],
+                     "updates_per_s": w["N"] * (w["n_real"] + w["n_cont"]) / wall}
+    out["decimation_ms_per_plan"] = (out["general"]["compute_ms"] - out["general"]["sweep_ms"]) - \
+        (out["circulant"]["compute_ms"] - out["circulant"]["sweep_ms"])
+    out["energies_x_leads"] = 2 * (w["n_real"] + w["n_cont"])
+    return out
