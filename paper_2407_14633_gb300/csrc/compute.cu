@@ -20,8 +20,11 @@ namespace {
 
 int kernel_class(const Dev* d) { return d->block == 1 ? 0 : (d->block == 2 ? 1 : 2); }
 
-// threads per CTA of the thread-per-lane (1 x 1, 2 x 2) sweeps: eight warps, one item each
-constexpr int CHAIN_BLOCK_THREADS = 256;
+// threads per CTA of the thread-per-lane (1 x 1, 2 x 2) sweeps: two warps, one item each.
+// Small CTAs spread a batch evenly over the SMs: 2048 items in 8-warp CTAs left 104 SMs with
+// two CTAs and 48 with one (the eight-device mode-space case ran 10% faster at two warps)
+constexpr int CHAIN_BLOCK_THREADS = 64;
+constexpr int CHAIN_WARPS = CHAIN_BLOCK_THREADS / 32;
 
 }  // namespace
 
@@ -704,7 +707,7 @@ static int mixed_recompute(Ctx* c, Plan& P) {
     if (redo[g].empty()) continue;
     const int cls = group_class(g);
     const int n = (int)redo[g].size();
-    const int grid = std::max(1, std::min(P.grid[g + 5], cls < 2 ? (n + 7) / 8 : n));
+    const int grid = std::max(1, std::min(P.grid[g + 5], cls < 2 ? (n + CHAIN_WARPS - 1) / CHAIN_WARPS : n));
     // the flagged energies are usually a fraction of a wave: spread them over wider CTAs
     // when that still holds them all at once (else the FP64 group's own width)
     const int w = (cls == 2 && c->opts.blk_warps == 0) ? partial_wave_width(c, false, P.gb[g], P.gm[g], n) : 0;

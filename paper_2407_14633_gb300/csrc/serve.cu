@@ -244,7 +244,8 @@ int step_locked(Ctx* c, Serve* s, int* n_active) {
       continue;
     }
     const size_t need = request_bytes(*r);
-    // room for one resident block of forward-sweep staging (8 warps x L layers x 1280 B)
+    // room for eight warps of forward-sweep staging (8 x L layers x 1280 B; at least one
+    // resident CTA of the thread-per-lane sweep)
     size_t Lmax = r->N;
     for (Req* q : s->active) Lmax = std::max<size_t>(Lmax, q->N);
     const size_t stage_min = Lmax * 8 * 5 * 32 * 8;
