@@ -20,6 +20,8 @@ namespace negf {
 
 namespace {
 
+// threads per CTA (one CTA per SM: its 2m x 2m matrices fill most of the shared memory).  The
+// decimation is bound by the sequential pivot steps of its inverses; 512 threads were no faster.
 constexpr int GT = 256;
 
 __device__ __forceinline__ cd cconj(cd a) { return mk(a.re, -a.im); }
@@ -97,7 +99,7 @@ __device__ __forceinline__ cd rowcol(const cd* X, const cd* Y, int i, int j, int
   return v;
 }
 
-__global__ void __launch_bounds__(GT) lead_general_kernel(const GenLeadJob* jobs, int* status) {
+__global__ void __launch_bounds__(GT, 1) lead_general_kernel(const GenLeadJob* jobs, int* status) {
   const GenLeadJob& J = jobs[blockIdx.y];
   const int e = blockIdx.x;
   if (e >= J.n_real + J.n_cont) return;
