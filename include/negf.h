@@ -80,7 +80,11 @@ typedef struct negf_ctx negf_ctx;
  * 28, else 4), 1 / 2 / 4 = that width.  Results are bitwise the same for every width.  blk_ctas_per_sm: cap on the resident CTAs per SM of
  * that sweep (0 = as many as fit); the grid is the cap times the SMs.  general_update: 1 =
  * never use the complex-symmetric form of the G_ll update, even for chains whose blocks and
- * lead rows are real (0 = use it there). */
+ * lead rows are real (0 = use it there).  chain_warps: CTA width (warps, one 32-energy item each) of
+ * the thread-per-lane sweeps of 1 x 1 and 2 x 2 blocks: 0 = autotuned when blk_warps is 0 (every
+ * width of 1, 2, 4, 8 warps timed once on the first group of at least one item per SM, per kernel
+ * class, element type and power-of-two bucket of the item count, then cached; else 2), 1 / 2 /
+ * 4 / 8 = that width.  Results are bitwise the same for every width. */
 typedef struct {
   int device_ordinal;
   void* stream;
@@ -93,6 +97,7 @@ typedef struct {
   int blk_warps;
   int blk_ctas_per_sm;
   int general_update;
+  int chain_warps;
 } negf_opts;
 
 /* Create / destroy a context on one GPU.  opts may be NULL (defaults: device 0, own
@@ -498,6 +503,9 @@ int negf_sweep_lanes(negf_ctx* ctx, uint64_t lanes[4]);
  * sites in FP64 (fp32 = 0) or FP32 (fp32 = 1): CTA width in warps and resident CTAs per SM
  * (ctas_per_sm may be NULL); NEGF_EINVAL if that shape was not tuned. */
 int negf_blk_width(negf_ctx* ctx, int fp32, int b, int m, int* warps, int* ctas_per_sm);
+/* The CTA width (warps) the autotuner last chose for the thread-per-lane sweep of blocks of
+ * width `block` (1 or 2) in FP64 (fp32 = 0) or FP32 (fp32 = 1); NEGF_EINVAL if none was tuned. */
+int negf_chain_width(negf_ctx* ctx, int fp32, int block, int* warps);
 
 /* Measured FP64 FMA throughput of this GPU (TFLOP/s): a register-resident FMA loop over
  * every SM, best of three, for the FP64 roofline of the sweep kernels. */

@@ -434,9 +434,9 @@ int negf_create(negf_ctx** out, const negf_opts* opts) {
   negf_ctx* c = new (std::nothrow) negf_ctx();
   if (!c) return NEGF_ENOMEM;
   if (opts) c->opts = *opts;
-  const int bw = c->opts.blk_warps;
+  const int bw = c->opts.blk_warps, cw = c->opts.chain_warps;
   if (c->opts.precision < 0 || c->opts.precision > 2 || !(bw == -1 || bw == 0 || bw == 1 || bw == 2 || bw == 4) ||
-      c->opts.blk_ctas_per_sm < 0) {
+      c->opts.blk_ctas_per_sm < 0 || !(cw == 0 || cw == 1 || cw == 2 || cw == 4 || cw == 8)) {
     delete c;
     return NEGF_EINVAL;
   }

@@ -20,11 +20,19 @@ namespace {
 
 int kernel_class(const Dev* d) { return d->block == 1 ? 0 : (d->block == 2 ? 1 : 2); }
 
-// threads per CTA of the thread-per-lane (1 x 1, 2 x 2) sweeps: two warps, one item each.
-// Small CTAs spread a batch evenly over the SMs: 2048 items in 8-warp CTAs left 104 SMs with
-// two CTAs and 48 with one (the eight-device mode-space case ran 10% faster at two warps)
-constexpr int CHAIN_BLOCK_THREADS = 64;
-constexpr int CHAIN_WARPS = CHAIN_BLOCK_THREADS / 32;
+// CTA width (warps, one item each) of the thread-per-lane (1 x 1, 2 x 2) sweeps when the
+// autotuner has not picked one: small CTAs spread a batch evenly over the SMs (2048 items in
+// 8-warp CTAs left 104 SMs with two CTAs and 48 with one; the eight-device mode-space case ran
+// 10% faster at two warps).  Groups of at least one item per SM are tuned over 1, 2, 4, 8 warps.
+constexpr int CHAIN_WARPS_DEFAULT = 2;
+size_t chain_smem(int warps) { return (size_t)warps * 32 * 33 * sizeof(double); }
+// tuning key of a thread-per-lane group: item counts are bucketed by powers of two, so a serving
+// loop whose batch changes step by step tunes once per bucket
+int chain_bucket(int n) {
+  int b = 0;
+  while ((1 << (b + 1)) <= n) ++b;
+  return b;
+}
 
 }  // namespace
 
@@ -264,6 +272,71 @@ static int tune_width(Ctx* c, Plan& P, int g) {
   return NEGF_OK;
 }
 
+// CTA width of a thread-per-lane group (g of class 0 or 1): every width of 1, 2, 4, 8 warps
+// runs the whole group once under events (at the most resident CTAs the staging holds, one item
+// per warp), the fastest is cached per (class, element type, item-count bucket).  The trials
+// write the same outputs as the real launch.
+static int tune_chain_width(Ctx* c, Plan& P, int g) {
+  const PlanBufs& B = *P.bufs;
+  const int cls = group_class(g);
+  const bool f32 = group_f32(g);
+  const int n = P.ncls[g];
+  const long long max_warps = P.stride[g] > 0 ? (long long)(B.stage.bytes / P.stride[g]) : 0;
+  struct Cand {
+    int w, grid;
+  };
+  std::vector<Cand> cand;
+  for (int w : {1, 2, 4, 8}) {
+    const int occ = sweep_chain_occupancy_t(f32, cls, 32 * w, chain_smem(w));
+    const long long grid = std::min<long long>(std::min<long long>((long long)c->sms * occ, (n + w - 1) / w),
+                                               max_warps / w);
+    if (grid >= 1) cand.push_back({w, (int)grid});
+  }
+  if (cand.empty()) return NEGF_OK;
+  cudaStream_t s = c->stream;
+  const int* order = (const int*)B.order.p + P.ooff[g];
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_err(c, NEGF_ECUDA, "event creation failed");
+  int rc = NEGF_OK;
+  {   // load the kernel once
+    const SweepArgs a = group_args(P, g, order, 1, nullptr, nullptr);
+    if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess ||
+        (cls == 0 ? (f32 ? launch_sweep_b1_f32(a, 1, 32, s) : launch_sweep_b1_f64(a, 1, 32, s))
+                  : (f32 ? launch_sweep_b2_f32(a, 1, 32, s) : launch_sweep_b2_f64(a, 1, 32, s))))
+      rc = set_err(c, NEGF_ECUDA, "tuning launch failed");
+    ++c->launches;
+  }
+  float best = 0.0f;
+  int bi = -1;
+  for (size_t i = 0; i < cand.size() && !rc; ++i) {
+    const SweepArgs a = group_args(P, g, order, n, nullptr, nullptr);
+    const int blk = 32 * cand[i].w;
+    if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+        (cls == 0 ? (f32 ? launch_sweep_b1_f32(a, cand[i].grid, blk, s) : launch_sweep_b1_f64(a, cand[i].grid, blk, s))
+                  : (f32 ? launch_sweep_b2_f32(a, cand[i].grid, blk, s) : launch_sweep_b2_f64(a, cand[i].grid, blk, s))) ||
+        cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = set_err(c, NEGF_ECUDA, "tuning launch failed");
+      break;
+    }
+    ++c->launches;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (bi < 0 || ms < best) {
+      best = ms;
+      bi = (int)i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  c->chain_tuned[std::make_tuple(cls, (int)f32, chain_bucket(n))] = cand[bi].w;
+  c->chain_last[std::make_tuple(cls, (int)f32)] = cand[bi].w;
+  P.gw[g] = cand[bi].w;
+  P.grid[g] = cand[bi].grid;
+  return NEGF_OK;
+}
+
 int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOverride>* ov, int chain_only,
                Plan& P, PlanBufs* bufs) {
   cudaSetDevice(c->ordinal);
@@ -401,9 +474,22 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     }
   }
 
+  // CTA width of the thread-per-lane groups: cached from an earlier tuning, tuned at the end of
+  // this call (a group of at least one item per SM, autotuning on, not under capture), or the
+  // default
+  bool tune_chain[NGROUPS] = {false};
+  for (int g = 0; g < NGROUPS; ++g) {
+    if (group_class(g) == 2 || !P.ncls[g]) continue;
+    P.gw[g] = c->opts.chain_warps > 0 ? c->opts.chain_warps : CHAIN_WARPS_DEFAULT;
+    if (c->opts.chain_warps > 0 || c->opts.blk_warps != 0) continue;
+    auto it = c->chain_tuned.find(std::make_tuple(group_class(g), (int)group_f32(g), chain_bucket(P.ncls[g])));
+    if (it != c->chain_tuned.end())
+      P.gw[g] = it->second;
+    else if (P.ncls[g] >= c->sms && capst == cudaStreamCaptureStatusNone)
+      tune_chain[g] = true;
+  }
+
   // launch geometry and staging per group (staging sized for FP64 elements)
-  P.block_threads = CHAIN_BLOCK_THREADS;
-  const size_t csmem = (size_t)(CHAIN_BLOCK_THREADS / 32) * 32 * 33 * sizeof(double);
   long long stage_bytes = 0;
   for (int g = 0; g < NGROUPS; ++g) {
     const int cls = group_class(g);
@@ -416,8 +502,14 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     const bool f32 = group_f32(g);
     int per_sm, wpb;
     if (cls < 2) {
-      per_sm = sweep_chain_occupancy_t(f32, cls, CHAIN_BLOCK_THREADS, csmem);
-      wpb = CHAIN_BLOCK_THREADS / 32;
+      per_sm = sweep_chain_occupancy_t(f32, cls, 32 * P.gw[g], chain_smem(P.gw[g]));
+      wpb = P.gw[g];
+      if (tune_chain[g])   // staging for the most resident warps of any trial width
+        for (int w : {1, 2, 4, 8}) {
+          const int occ = sweep_chain_occupancy_t(f32, cls, 32 * w, chain_smem(w));
+          const long long warps = std::min<long long>((long long)c->sms * occ * w, ((P.ncls[g] + w - 1) / w) * (long long)w);
+          stage_bytes = std::max(stage_bytes, P.stride[g] * warps);
+        }
     } else {
       const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16, P.gw[g]);
       if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
@@ -441,14 +533,14 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     for (int g = 0; g < 5; ++g) {
       if (!P.ncls[g + 5]) continue;
       const int cls = group_class(g);
-      const int wpb = cls < 2 ? CHAIN_BLOCK_THREADS / 32 : 1;
+      const int wpb = cls < 2 ? P.gw[g + 5] : 1;
       stage_bytes = std::max(stage_bytes, P.stride[g] * (long long)P.grid[g + 5] * wpb);
       if (cls == 2) {
         const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], 16, P.gw[g]);
         if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
         sweep_blk_occupancy_t(false, P.gw[g], P.gb[g], P.gm[g]);
       } else {
-        sweep_chain_occupancy_t(false, cls, CHAIN_BLOCK_THREADS, csmem);
+        sweep_chain_occupancy_t(false, cls, 32 * P.gw[g + 5], chain_smem(P.gw[g + 5]));
       }
     }
 
@@ -489,7 +581,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       stage_bytes = 0;
       for (int g = 0; g < NGROUPS; ++g) {
         if (!P.ncls[g]) continue;
-        const int wpb = group_class(g) < 2 ? CHAIN_BLOCK_THREADS / 32 : 1;
+        const int wpb = group_class(g) < 2 ? P.gw[g] : 1;
         // an FP32 group's grid also runs its FP64 recompute, with the FP64 stride
         const long long per = std::max(P.stride[g], P.stride[g % 5]) * wpb;
         const long long fit = per > 0 ? cap / per : 1;
@@ -641,6 +733,11 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       int rc = tune_width(c, P, g);
       if (rc) return rc;
     }
+  for (int g = 0; g < NGROUPS; ++g)
+    if (tune_chain[g]) {
+      int rc = tune_chain_width(c, P, g);
+      if (rc) return rc;
+    }
   return NEGF_OK;
 }
 
@@ -653,9 +750,11 @@ static int launch_group(Ctx* c, const Plan& P, int g, const int* order, int n, i
   cudaStream_t s = c->stream;
   int rc;
   if (cls == 0)
-    rc = f32 ? launch_sweep_b1_f32(a, grid, P.block_threads, s) : launch_sweep_b1_f64(a, grid, P.block_threads, s);
+    rc = f32 ? launch_sweep_b1_f32(a, grid, 32 * (warps > 0 ? warps : P.gw[g]), s)
+             : launch_sweep_b1_f64(a, grid, 32 * (warps > 0 ? warps : P.gw[g]), s);
   else if (cls == 1)
-    rc = f32 ? launch_sweep_b2_f32(a, grid, P.block_threads, s) : launch_sweep_b2_f64(a, grid, P.block_threads, s);
+    rc = f32 ? launch_sweep_b2_f32(a, grid, 32 * (warps > 0 ? warps : P.gw[g]), s)
+             : launch_sweep_b2_f64(a, grid, 32 * (warps > 0 ? warps : P.gw[g]), s);
   else
     rc = launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], grid, warps > 0 ? warps : P.gw[g], s);
   if (rc) return set_err(c, NEGF_ECUDA, "sweep launch failed");
@@ -707,10 +806,14 @@ static int mixed_recompute(Ctx* c, Plan& P) {
     if (redo[g].empty()) continue;
     const int cls = group_class(g);
     const int n = (int)redo[g].size();
-    const int grid = std::max(1, std::min(P.grid[g + 5], cls < 2 ? (n + CHAIN_WARPS - 1) / CHAIN_WARPS : n));
+    // a thread-per-lane recompute runs at the FP32 group's CTA width and grid, which its
+    // staging was sized for
+    const int cw = cls < 2 ? P.gw[g + 5] : 1;
+    const int grid = std::max(1, std::min(P.grid[g + 5], cls < 2 ? (n + cw - 1) / cw : n));
     // the flagged energies are usually a fraction of a wave: spread them over wider CTAs
     // when that still holds them all at once (else the FP64 group's own width)
-    const int w = (cls == 2 && c->opts.blk_warps == 0) ? partial_wave_width(c, false, P.gb[g], P.gm[g], n) : 0;
+    const int w = cls < 2 ? cw
+                          : ((c->opts.blk_warps == 0) ? partial_wave_width(c, false, P.gb[g], P.gm[g], n) : 0);
     int rc = launch_group(c, P, g, (const int*)B.order2.p + off[g], n, grid, nullptr, nullptr, w);
     if (rc) return rc;
   }
@@ -1116,6 +1219,14 @@ int negf_kernel_time(negf_ctx* c, double* sweep_ms, uint64_t* sweeps) {
   *sweeps = c->prof_count;
   c->prof_ms = 0.0;
   c->prof_count = 0;
+  return NEGF_OK;
+}
+
+int negf_chain_width(negf_ctx* c, int fp32, int block, int* warps) {
+  if (!c || !warps || (block != 1 && block != 2)) return NEGF_EINVAL;
+  auto it = c->chain_last.find(std::make_tuple(block == 1 ? 0 : 1, fp32 ? 1 : 0));
+  if (it == c->chain_last.end()) return NEGF_EINVAL;
+  *warps = it->second;
   return NEGF_OK;
 }
 

@@ -120,6 +120,10 @@ struct Ctx {
   // wide-block sweep, keyed by (element type, b, m, items); the latest per (type, b, m)
   std::map<std::tuple<int, int, int, int>, std::pair<int, int>> blk_tuned;
   std::map<std::tuple<int, int, int>, std::pair<int, int>> blk_last;
+  // CTA width (warps) of the thread-per-lane sweeps chosen by the autotuner, keyed by (kernel
+  // class, element type, item-count bucket); the latest per (class, element type)
+  std::map<std::tuple<int, int, int>, int> chain_tuned;
+  std::map<std::tuple<int, int>, int> chain_last;
   // serving state (serve.cu)
   struct Serve* serve = nullptr;
   std::mutex serve_mu;

@@ -15,6 +15,8 @@
 //   c_l = |G_{l,L-1}|^2 = |gL_l|^2 |h_l|^2 c_{l+1},  c_{L-1} = |G_{L-1,L-1}|^2,
 //   G_{l,l} = gL_l + gL_l^2 |h_l|^2 G_{l+1,l+1},
 //   A_S,ll = Gamma_S q_l |G_ll|^2, A_D,ll = Gamma_D c_l, T = Gamma_S Gamma_D c_0.
+#include <algorithm>
+
 #include "common.cuh"
 #include "lead.cuh"
 
@@ -440,7 +442,9 @@ int sweep_chain_occupancy(int cls, int threads, size_t smem) {
 int sweep_chain_occupancy_t(bool fp32, int cls, int threads, size_t smem) {
   void (*k)(SweepArgs) = fp32 ? (cls == 0 ? sweep_b1_kernel<float> : sweep_b2_kernel<float>)
                               : (cls == 0 ? sweep_b1_kernel<double> : sweep_b2_kernel<double>);
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the limit covers the widest CTA (8 warps), so a launch of any tuned width fits under it
+  const size_t widest = (size_t)8 * 32 * 33 * sizeof(double);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max(smem, widest));
   int per = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem) != cudaSuccess || per < 1) {
     cudaGetLastError();

@@ -25,7 +25,7 @@ class Opts(C.Structure):
     _fields_ = [("device_ordinal", C.c_int), ("stream", C.c_void_p), ("hbm_budget_bytes", C.c_size_t),
                 ("precision", C.c_int), ("flag_threshold", C.c_double), ("edge_window", C.c_double),
                 ("fault_alloc_after", C.c_int), ("growth_threshold", C.c_double), ("blk_warps", C.c_int),
-                ("blk_ctas_per_sm", C.c_int), ("general_update", C.c_int)]
+                ("blk_ctas_per_sm", C.c_int), ("general_update", C.c_int), ("chain_warps", C.c_int)]
 
 
 class Lead(C.Structure):
@@ -130,6 +130,7 @@ _PROTOS = {
     "negf_fp64_peak": (C.c_int, [C.c_void_p, _dp]),
     "negf_sweep_lanes": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "negf_blk_width": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, _ip, _ip]),
+    "negf_chain_width": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip]),
     "negf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)]),
     "negf_serve_step": (C.c_int, [C.c_void_p, _ip]),
     "negf_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(ScResult)]),
@@ -242,10 +243,10 @@ class Context:
 
     def __init__(self, device=0, stream=None, hbm_budget=0, precision=PREC_FP64, flag_threshold=0.0,
                  edge_window=0.0, fault_alloc_after=0, growth_threshold=0.0, blk_warps=0, blk_ctas_per_sm=0,
-                 general_update=0):
+                 general_update=0, chain_warps=0):
         self.lib = load()
         o = Opts(device, stream or 0, hbm_budget, precision, flag_threshold, edge_window, fault_alloc_after,
-                 growth_threshold, blk_warps, blk_ctas_per_sm, general_update)
+                 growth_threshold, blk_warps, blk_ctas_per_sm, general_update, chain_warps)
         h = C.c_void_p()
         rc = self.lib.negf_create(C.byref(h), C.byref(o))
         if rc:
@@ -562,6 +563,12 @@ class Context:
         """CTA width chosen by the autotuner for ring blocks of width b (None if not tuned)."""
         s = self.blk_shape(b, m, fp32)
         return s[0] if s else None
+
+    def chain_width(self, block=1, fp32=False):
+        """CTA width (warps) the autotuner chose for the thread-per-lane sweep (None if not tuned)."""
+        w = C.c_int()
+        rc = self.lib.negf_chain_width(self.h, 1 if fp32 else 0, block, C.byref(w))
+        return w.value if rc == OK else None
 
     def blk_shape(self, b, m, fp32=False):
         """(CTA width, resident CTAs per SM) chosen by the autotuner (None if not tuned)."""

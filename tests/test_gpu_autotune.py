@@ -47,3 +47,38 @@ def test_autotuner_records_width_and_matches_oracle():
     o = run_oracle(p, chunk=32)
     assert rel_inf(r["n"], o["n"]) < 1e-10
     assert rel_inf(r["T"], o["T"]) < 1e-10
+
+
+def _run_mode(**kw):
+    from paper_2407_14633_gb300 import negf
+    # two mode-space devices, two subbands each, 4096 + 64 energies: 260 thread-per-lane items
+    # per kernel class (more than one per SM, so the autotuner tunes), 1 x 1 and 2 x 2 blocks
+    with negf.Context(**kw) as ctx:
+        devs = []
+        for N, cells in ((60, False), (48, True)):
+            U = synth.ramp_barrier(N, drop=0.2, height=0.1, width=N / 6.0)
+            d = lib_device(ctx, "mode", 17, -2.7, N, 0.0, -0.2, (6, 5), cells)
+            ctx.set_potential(d, U)
+            ctx.set_grid_spec(d, 0.0, -0.2, 0.025, 1e-6, -10.0, 4096, 64)
+            devs.append(d)
+        r = ctx.compute(devs)
+        # under the FP32 policy every lane (contour too) runs in complex64
+        fp32 = kw.get("precision", negf.PREC_FP64) == negf.PREC_FP32
+        return r, ctx.chain_width(1, fp32), ctx.chain_width(2, fp32)
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+def test_chain_width_does_not_change_results(fp32):
+    from paper_2407_14633_gb300 import negf
+    prec = negf.PREC_FP32 if fp32 else negf.PREC_FP64
+    ref, _, _ = _run_mode(precision=prec, chain_warps=2)
+    for w in (1, 4, 8):
+        r, _, _ = _run_mode(precision=prec, chain_warps=w)
+        for a, b in zip(r, ref):
+            for k in ("n", "T", "n_cont", "n_real"):
+                assert np.array_equal(a[k], b[k]), (w, k)
+            assert a["I"] == b["I"]
+    tuned, w1, w2 = _run_mode(precision=prec)
+    assert w1 in (1, 2, 4, 8) and w2 in (1, 2, 4, 8)
+    for a, b in zip(tuned, ref):
+        assert np.array_equal(a["n"], b["n"]) and np.array_equal(a["T"], b["T"])
