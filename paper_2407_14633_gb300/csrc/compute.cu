@@ -485,7 +485,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     auto it = c->chain_tuned.find(std::make_tuple(group_class(g), (int)group_f32(g), chain_bucket(P.ncls[g])));
     if (it != c->chain_tuned.end())
       P.gw[g] = it->second;
-    else if (P.ncls[g] >= c->sms && capst == cudaStreamCaptureStatusNone)
+    else if (P.ncls[g] >= c->sms && capst == cudaStreamCaptureStatusNone && !c->chain_tuning_off)
       tune_chain[g] = true;
   }
 

@@ -124,6 +124,9 @@ struct Ctx {
   // class, element type, item-count bucket); the latest per (class, element type)
   std::map<std::tuple<int, int, int>, int> chain_tuned;
   std::map<std::tuple<int, int>, int> chain_last;
+  // set while the serving loop plans a step: its batch changes every few steps, and a trial of
+  // every width at each new item-count bucket cost more than it saved (the default is kept)
+  bool chain_tuning_off = false;
   // serving state (serve.cu)
   struct Serve* serve = nullptr;
   std::mutex serve_mu;

@@ -235,7 +235,9 @@ int negf_sc_solve_multi(negf_ctx* c, const int* devs, int C, const negf_bias* bi
     if (launch_broyden(dsc, 1, c->stream)) return set_err(c, NEGF_ECUDA, "broyden launch failed");
     return NEGF_OK;
   };
-  uint64_t per_iter = 4;
+  // launches per captured iteration: Poisson, prep of 1 x 1 chains, sweep groups, second stage,
+  // gather, Broyden (an uncaptured iteration counts the plan's own launches in launch_plan)
+  uint64_t per_iter = 4 + (plan.n_prep > 0 ? 1 : 0);
   for (int g = 0; g < NGROUPS; ++g) per_iter += (plan.ncls[g] > 0);
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
     const uint64_t l0 = c->launches;
@@ -252,11 +254,12 @@ int negf_sc_solve_multi(negf_ctx* c, const int* devs, int C, const negf_bias* bi
   for (int it = 0; it < M && st == 0; ++it) {
     if (exec) {
       if (cudaGraphLaunch(exec, c->stream) != cudaSuccess) rc = set_err(c, NEGF_ECUDA, "graph launch failed");
+      c->launches += per_iter;
     } else {
       rc = iteration();
+      c->launches += 3;
     }
     if (rc) break;
-    c->launches += per_iter;
     if (cudaMemcpyAsync(h_state, bstate.p, 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
       rc = set_err(c, NEGF_ECUDA, "self-consistent iteration failed");

@@ -290,7 +290,9 @@ int step_locked(Ctx* c, Serve* s, int* n_active) {
     s->drop_graph();
     std::vector<Dev*> devs;
     for (Req* r : s->active) devs.push_back(find_device(c, r->dev));
+    c->chain_tuning_off = true;
     int rc = build_plan(c, devs, nullptr, -1, s->plan, &s->bufs);
+    c->chain_tuning_off = false;
     if (rc) return rc;
     std::vector<ScDev> sds;
     for (Req* r : s->active) sds.push_back(r->sd);
