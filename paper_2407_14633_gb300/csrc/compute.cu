@@ -273,9 +273,11 @@ static int tune_width(Ctx* c, Plan& P, int g) {
 }
 
 // CTA width of a thread-per-lane group (g of class 0 or 1): every width of 1, 2, 4, 8 warps
-// runs the whole group once under events (at the most resident CTAs the staging holds, one item
-// per warp), the fastest is cached per (class, element type, item-count bucket).  The trials
-// write the same outputs as the real launch.
+// runs the whole group twice under events (at the most resident CTAs the staging holds, one
+// item per warp; the faster run counts), and the fastest width is cached per (class, element
+// type, item-count bucket) if it beats the default width by more than 3%: smaller differences
+// between widths are within the run-to-run spread of these sweeps.  The trials write the same
+// outputs as the real launch.
 static int tune_chain_width(Ctx* c, Plan& P, int g) {
   const PlanBufs& B = *P.bufs;
   const int cls = group_class(g);
@@ -307,9 +309,9 @@ static int tune_chain_width(Ctx* c, Plan& P, int g) {
       rc = set_err(c, NEGF_ECUDA, "tuning launch failed");
     ++c->launches;
   }
-  float best = 0.0f;
-  int bi = -1;
-  for (size_t i = 0; i < cand.size() && !rc; ++i) {
+  std::vector<float> tbest(cand.size(), -1.0f);
+  for (size_t t = 0; t < 2 * cand.size() && !rc; ++t) {
+    const size_t i = t % cand.size();
     const SweepArgs a = group_args(P, g, order, n, nullptr, nullptr);
     const int blk = 32 * cand[i].w;
     if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
@@ -322,14 +324,17 @@ static int tune_chain_width(Ctx* c, Plan& P, int g) {
     ++c->launches;
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, e0, e1);
-    if (bi < 0 || ms < best) {
-      best = ms;
-      bi = (int)i;
-    }
+    if (tbest[i] < 0.0f || ms < tbest[i]) tbest[i] = ms;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
+  int bi = 0, di = -1;
+  for (size_t i = 0; i < cand.size(); ++i) {
+    if (tbest[i] < tbest[bi]) bi = (int)i;
+    if (cand[i].w == CHAIN_WARPS_DEFAULT) di = (int)i;
+  }
+  if (di >= 0 && bi != di && !(tbest[bi] < 0.97f * tbest[di])) bi = di;
   c->chain_tuned[std::make_tuple(cls, (int)f32, chain_bucket(n))] = cand[bi].w;
   c->chain_last[std::make_tuple(cls, (int)f32)] = cand[bi].w;
   P.gw[g] = cand[bi].w;

@@ -74,9 +74,12 @@ def batched_uneven(reps=3):
                 res = ctx.compute(devs)
             wall = (time.perf_counter() - t0) / reps
             ms, k = ctx.kernel_time()
+            fp32 = prec == negf.PREC_FP32
+            widths = {"1x1": ctx.chain_width(1, fp32), "2x2": ctx.chain_width(2, fp32)}
         sweep_s = ms / max(k, 1) * 1e-3
         entry = {"updates_per_s_sweep": units / sweep_s, "sweep_ms": sweep_s * 1e3,
-                 "updates_per_s_e2e": units / wall, "e2e_ms": wall * 1e3, "setup_s": t_setup}
+                 "updates_per_s_e2e": units / wall, "e2e_ms": wall * 1e3, "setup_s": t_setup,
+                 "cta_warps": widths}
         if ref is None:
             ref = res
         else:
@@ -385,6 +388,7 @@ def multichannel(M=40, tol=1e-6):
         one = ctx.sc_solve(devs[0], w["V_DS"], w["V_GS"], w["U0"][0], kappa, M=M, tol=tol, check=False)
         wall1 = time.perf_counter() - t0
         out["twenty_100nm"] = {
+            "cta_warps": ctx.chain_width(1),
             "converged": r["converged"], "iterations": r["iterations"], "seconds": wall,
             "ms_per_iteration": wall / r["iterations"] * 1e3,
             "updates_per_s": w["n_tubes"] * w["N"] * lanes * r["iterations"] / wall,
