@@ -170,7 +170,7 @@ struct Plan {
   std::vector<int> it0;
   std::vector<long long> tbase;
   int prec = NEGF_PREC_FP64;
-  int n_items = 0, block_threads = 256;
+  int n_items = 0;
   int grid[NGROUPS] = {0}, ooff[NGROUPS] = {0}, ncls[NGROUPS] = {0};
   int gb[NGROUPS] = {0}, gm[NGROUPS] = {0}, gw[NGROUPS] = {0};   // bmax, mmax, warps of wide-block groups
   int gcap[NGROUPS] = {0};                                          // tuned resident CTAs per SM (0: rule)
