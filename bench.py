@@ -350,7 +350,7 @@ def run_ours(args):
                 "mixed_precision": workloads.mixed_precision, "serving": workloads.serving_sweep,
                 "gate_sweep": lambda: {"warm": workloads.gate_sweep(), "cold": workloads.gate_sweep(warm=False)},
                 "adaptive_grid": workloads.adaptive_grid, "multichannel": workloads.multichannel,
-                "general_leads": workloads.general_leads}
+                "general_leads": workloads.general_leads, "paper_scaling": workloads.paper_scaling}
         pick = list(runs) if args.extras == "all" else args.extras.split(",")
         line["extras"] = {k: runs[k]() for k in pick}
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -426,7 +426,7 @@ def main():
     ap.add_argument("--extras", nargs="?", const="all", default=None,
                     help="also run the small, batched-uneven, mixed-precision, serving and gate-sweep workloads "
                          "(or a comma list of modespace_small, batched_uneven, mixed_precision, serving, "
-                         "gate_sweep, adaptive_grid, multichannel, general_leads)")
+                         "gate_sweep, adaptive_grid, multichannel, general_leads, paper_scaling)")
     ap.add_argument("--profile-small", action="store_true",
                     help="reduced case of the block sweep for ncu captures")
     ap.add_argument("--blk-warps", type=int, default=1,

@@ -26,6 +26,9 @@ nanotube transistors, Sec. 3.1-3.3):
 * ``adaptive_lengths``  (17,0) mode-space channels of 224, 736 and 1760 rings (23.9, 78.4 and
   187.4 nm, the lengths of Sec. 3.3), subband j = 6, drain ramp 0 -> -0.4 eV plus a 0.1 eV
   barrier, V_DS = 0.4 V: quadrature error of the real-axis charge against the point count.
+* ``paper_scaling``     the shapes of the paper's timing tables, for context: one doubly
+  degenerate (17,0) subband (j = 6) at N = 512 ... 4096 rings with 11,904 + 96 energies
+  (Table 1), and N = 524,288 rings with 90 contour nodes and 1, 2, 4, 8 subbands (Table 2).
 * ``planar_array``      tubes side by side sharing contacts and gate (Sec. 3.4): five 96-ring
   (10 nm) tubes at zero bias, and twenty 940-ring (100 nm) tubes at V_DS = 0.1 V, subbands
   j = 6, 5, 2048 + 64 energies, contacts 1 eV below midgap; neighbouring tubes coupled with
@@ -184,3 +187,12 @@ def general_lead(m, seed, t=T_HOP, onsite=0.3, disorder=0.4):
     T2 = 0.8 * t * np.eye(m) + pert(True)
     tau = 0.9 * t * np.eye(m) + pert(False)
     return dict(T1=T1, T2=T2, tau=tau.astype(complex), H0=herm(), H1=herm())
+
+
+def paper_scaling():
+    """Workload shapes of the paper's timing tables (Sec. 3.2), for context timings."""
+    return dict(name="paper_scaling", n_tube=N_TUBE, t=T_HOP, kT=KT, eta=ETA,
+                table1=dict(N=(512, 1024, 2048, 4096), modes=(6,), n_real=11904, n_cont=96, V_DS=0.1,
+                            paper_s=(2.04, 3.12, 5.28, 8.76), paper_gpus=(64, 128, 256, 512)),
+                table2=dict(N=524288, modes=((6,), (6, 5), (6, 5, 7, 4), (6, 5, 7, 4, 8, 3, 9, 2)), n_cont=90,
+                            paper_s=(1.98, 2.75, 3.24, 5.63)))

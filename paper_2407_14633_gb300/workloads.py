@@ -430,3 +430,46 @@ def general_leads(reps=3):
         (out["circulant"]["compute_ms"] - out["circulant"]["sweep_ms"])
     out["energies_x_leads"] = 2 * (w["n_real"] + w["n_cont"])
     return out
+
+
+def paper_scaling(reps=2):
+    """Context against the paper's timing tables (A100, NERSC Perlmutter; the paper's NEGF puts
+    one thread per Green's-function column with a host recursion, Sec. 2.2.4).  Table 1: one
+    NEGF evaluation (negf_compute, sweeps + second stage) of a (17,0) tube with one doubly
+    degenerate subband, drain ramp 0 -> -0.1 eV, 11,904 Gauss-Legendre real-axis energies plus
+    96 contour nodes, N = 512 ... 4096.  Table 2: equilibrium-style evaluation of N = 524,288
+    rings on 90 contour nodes with 1, 2, 4, 8 subbands (no real-axis lanes)."""
+    w = synth.paper_scaling()
+    out = {"table1": [], "table2": []}
+    t1 = w["table1"]
+    for N, ps, ng in zip(t1["N"], t1["paper_s"], t1["paper_gpus"]):
+        with negf.Context() as ctx:
+            dev = ctx.device_create(N, block=1, rings_per_block=1, n_chains=len(t1["modes"]))
+            ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], list(t1["modes"]), 0.0, -t1["V_DS"])
+            ctx.set_potential(dev, synth.ramp_barrier(N, drop=t1["V_DS"], height=0.0))
+            ctx.set_grid_spec(dev, 0.0, -t1["V_DS"], w["kT"], w["eta"], -3.0 * abs(w["t"]) - 1.5, t1["n_real"],
+                              t1["n_cont"])
+            ctx.compute([dev])
+            ctx.profile(True)
+            ctx.kernel_time()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                ctx.compute([dev])
+            wall = (time.perf_counter() - t0) / reps
+            ms, k = ctx.kernel_time()
+        out["table1"].append({"N": N, "negf_ms": wall * 1e3, "sweep_ms": ms / max(k, 1),
+                              "paper_s": ps, "paper_a100s": ng})
+    t2 = w["table2"]
+    N = t2["N"]
+    for modes, ps in zip(t2["modes"], t2["paper_s"]):
+        with negf.Context() as ctx:
+            dev = ctx.device_create(N, block=1, rings_per_block=1, n_chains=len(modes))
+            ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], list(modes), 0.0, 0.0)
+            ctx.set_potential(dev, np.zeros(N))
+            ctx.set_grid_spec(dev, 0.0, 0.0, w["kT"], w["eta"], -3.0 * abs(w["t"]) - 1.0, 0, t2["n_cont"])
+            ctx.compute([dev])
+            t0 = time.perf_counter()
+            ctx.compute([dev])
+            wall = time.perf_counter() - t0
+        out["table2"].append({"modes": len(modes), "negf_ms": wall * 1e3, "paper_s": ps})
+    return out
