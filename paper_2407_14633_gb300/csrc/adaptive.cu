@@ -95,12 +95,14 @@ int set_adaptive(Ctx* c, Dev* d, const negf_grid_spec& spec, const negf_adaptive
   return NEGF_OK;
 }
 
-// Integrand of one ring per energy from the per-item partial ring sums of a one-energy-per-item
-// run with unit weights (item = chain * n_real + k): I_k = sum over chains, in chain order.
-// The peak is the largest I_k, the lowest k on ties: strided scan, then a fixed-shape tree.
-__global__ void __launch_bounds__(256) integrand_peak_kernel(const double* partial, int n_chains, int n_real,
-                                                             int N, int ring, const double* E, double* out,
-                                                             double* best) {
+// Integrand of one ring per energy, I_k = sum over chains in chain order, from either the
+// per-lane values the thread-per-lane sweeps captured at that ring (cap, slot chain * n_real + k)
+// or, for wider blocks, the per-item partial ring sums of a one-energy-per-item run (item =
+// chain * n_real + k); both with unit weights.  The peak is the largest I_k, the lowest k on
+// ties: strided scan, then a fixed-shape tree.
+__global__ void __launch_bounds__(256) integrand_peak_kernel(const double* partial, const double* cap,
+                                                             int n_chains, int n_real, int N, int ring,
+                                                             const double* E, double* out, double* best) {
   __shared__ double sv[256];
   __shared__ int sk[256];
   const int t = threadIdx.x;
@@ -108,7 +110,8 @@ __global__ void __launch_bounds__(256) integrand_peak_kernel(const double* parti
   int bk = 0x7fffffff;
   for (int k = t; k < n_real; k += blockDim.x) {
     double v = 0.0;
-    for (int ch = 0; ch < n_chains; ++ch) v += partial[((long long)ch * n_real + k) * N + ring];
+    for (int ch = 0; ch < n_chains; ++ch)
+      v += cap ? cap[(long long)ch * n_real + k] : partial[((long long)ch * n_real + k) * N + ring];
     if (out) out[k] = v;
     if (v > bv) {
       bv = v;
@@ -132,20 +135,24 @@ __global__ void __launch_bounds__(256) integrand_peak_kernel(const double* parti
   }
 }
 
-// One sweep of every real-axis energy of d (one lane each, unit weights, the device's
-// occupations and potential), then the integrand of `ring` (out, device, may be null) and its
-// peak into the context's refine buffer: best[0] = E_s, best[1] = index, then the unit weights
-// (written whenever the buffer grows, never overwritten).
+// One sweep of every real-axis energy of d (unit weights, the device's occupations and
+// potential), then the integrand of `ring` (out, device, may be null) and its peak into the
+// context's refine buffer: best[0] = E_s, best[1] = index, the unit weights (written whenever the
+// buffer grows, never overwritten), then the captured values.  Chains of 1 x 1 and 2 x 2 blocks
+// keep 32 energies per item and capture each lane's value at the ring; wider blocks run one
+// energy per item (their usual item) and read the per-item ring sums.
 int integrand_run(Ctx* c, Dev* d, int ring, double* out) {
   const int nr = d->n_real;
-  const size_t bytes = (size_t)(nr + 2) * sizeof(double);
+  const bool capture = d->block <= 2;
+  const size_t bytes = (size_t)(nr + 2 + (size_t)d->n_chains * nr) * sizeof(double);
   if (c->refine.bytes < bytes) {
-    std::vector<double> ones(nr + 2, 1.0);
+    std::vector<double> ones(nr + 2 + (size_t)d->n_chains * nr, 1.0);
     int rc = upload(c, c->refine, ones.data(), bytes);
     if (rc) return rc;
   }
   double* best = (double*)c->refine.p;
   const double* ones = best + 2;
+  double* cap = best + 2 + nr;
   ViewOverride o;
   o.n_real = nr;
   o.E = (const double*)d->dE.p;
@@ -154,15 +161,20 @@ int integrand_run(Ctx* c, Dev* d, int ring, double* out) {
   o.fD = (const double*)d->dfD.p;
   o.eta = d->eta;
   o.n_cont = 0;
-  o.one_energy_per_item = true;
+  o.one_energy_per_item = !capture;
   std::vector<Dev*> one{d};
   std::vector<ViewOverride> ov{o};
   Plan P;
   int rc = build_plan(c, one, &ov, -1, P);
   if (rc) return rc;
+  if (capture) {
+    P.ring_cap = cap;   // T slots of a one-device plan: chain * n_real + k
+    P.cap_ring = ring;
+  }
   if ((rc = launch_plan(c, P))) return rc;
-  integrand_peak_kernel<<<1, 256, 0, c->stream>>>((const double*)c->scratch.partial.p, d->n_chains, nr, d->n_rings,
-                                                  ring, (const double*)d->dE.p, out, best);
+  integrand_peak_kernel<<<1, 256, 0, c->stream>>>((const double*)c->scratch.partial.p, capture ? cap : nullptr,
+                                                  d->n_chains, nr, d->n_rings, ring, (const double*)d->dE.p, out,
+                                                  best);
   if (cudaGetLastError() != cudaSuccess) return set_err(c, NEGF_ECUDA, "integrand launch failed");
   ++c->launches;
   return NEGF_OK;

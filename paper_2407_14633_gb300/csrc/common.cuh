@@ -192,6 +192,10 @@ struct SweepArgs {
   long long stage_stride; // bytes per resident warp
   int* status;            // device error flag (0 ok)
   unsigned long long* lane_stats;  // per-form lane counts (profiling; may be null)
+  // thread-per-lane sweeps: each real-axis lane's weighted contribution at ring cap_ring, one
+  // slot per T slot (the integrand of the semi-adaptive grid); null when not wanted
+  double* ring_cap = nullptr;
+  int cap_ring = -1;
 };
 
 // ---------------------------------------------------------------- launchers

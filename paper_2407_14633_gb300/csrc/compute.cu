@@ -163,6 +163,8 @@ static SweepArgs group_args(const Plan& P, int g, const int* order, int n, doubl
   a.stage_stride = P.stride[g % 5];
   a.status = (int*)B.status.p;
   a.lane_stats = nullptr;
+  a.ring_cap = P.ring_cap;
+  a.cap_ring = P.cap_ring;
   return a;
 }
 

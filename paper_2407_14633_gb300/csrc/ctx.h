@@ -183,6 +183,8 @@ struct Plan {
   int recomputed = 0;
   bool want_diag = false;
   int n_prep = 0, prep_L = 0;             // prep_kernel descriptors and longest chain
+  double* ring_cap = nullptr;             // per-energy contributions at ring cap_ring (1 x 1, 2 x 2)
+  int cap_ring = -1;
 };
 int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOverride>* ov, int chain_only,
                Plan& P, PlanBufs* bufs = nullptr);

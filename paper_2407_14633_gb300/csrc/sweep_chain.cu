@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
       } else {
         v = kap.re * (double)G.im + kap.im * (double)G.re;
       }
+      if (a.ring_cap && l == a.cap_ring && W.kind == 0 && act) a.ring_cap[W.tout + lane] = v;
       red[(l & 31) * 33 + lane] = v;
       if ((l & 31) == 0) {
         const int cnt = min(32, L - l);
@@ -392,6 +393,8 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
       }
       // rings of the layer -> transpose slots ring & 31
       const int r0 = l * rpb;
+      if (a.ring_cap && W.kind == 0 && act && a.cap_ring >= r0 && a.cap_ring < r0 + rpb)
+        a.ring_cap[W.tout + lane] = rpb == 2 ? (a.cap_ring == r0 ? v0 : v1) : v0 + v1;
       if (rpb == 2) {
         red[(r0 & 31) * 33 + lane] = v0;
         red[((r0 + 1) & 31) * 33 + lane] = v1;
