@@ -88,3 +88,38 @@ def test_library_adaptive_grid_matches_oracle(lib, limits, dens):
     for k in ("E", "w", "fS", "fD"):
         assert np.max(np.abs(r[k] - o[k])) < 1e-13 * max(1.0, np.max(np.abs(o[k])))
     assert np.max(np.abs(r["c"] - o["c"])) < 1e-13 * np.max(np.abs(o["c"]))
+
+
+def test_struct_layouts_match_header(tmp_path):
+    # the ctypes structures of the binding must lay out exactly as the C structs of the header
+    import shutil
+    import subprocess
+    import ctypes as C
+    from paper_2407_14633_gb300 import negf
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"negf_opts": negf.Opts, "negf_lead": negf.Lead, "negf_lead_general": negf.LeadGeneral,
+               "negf_grid": negf.Grid, "negf_grid_spec": negf.GridSpec, "negf_adaptive": negf.Adaptive,
+               "negf_out": negf.Out, "negf_poisson": negf.Poisson, "negf_bias": negf.Bias,
+               "negf_broyden": negf.Broyden, "negf_request": negf.Request, "negf_sc_result": negf.ScResult}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "negf.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (cname, cname))
+        for fname, _ in py._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (cname, fname, cname, fname))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            a, b, v = ln.split()
+            got[(a, b)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
