@@ -84,7 +84,13 @@ typedef struct negf_ctx negf_ctx;
  * the thread-per-lane sweeps of 1 x 1 and 2 x 2 blocks: 0 = autotuned when blk_warps is 0 (every
  * width of 1, 2, 4, 8 warps timed once on the first group of at least one item per SM, per kernel
  * class, element type and power-of-two bucket of the item count, then cached; else 2), 1 / 2 /
- * 4 / 8 = that width.  Results are bitwise the same for every width. */
+ * 4 / 8 = that width.  Results are bitwise the same for every width.  long_chain_split: FP64
+ * sweeps of 1 x 1 chains split along the channel into segments of 512 layers, one warp per
+ * segment of 32 energies, joined by scans of the per-segment maps of the forward and backward
+ * recursions: 0 = for devices with at least 16384 layers and at most 128 such 32-energy items
+ * of their own (long channels, few energies), 1 = for every 1 x 1 chain, -1 = never.  The choice
+ * is made per device, so a device's results do not depend on its batch; they differ from the
+ * unsplit sweep by rounding only. */
 typedef struct {
   int device_ordinal;
   void* stream;
@@ -98,6 +104,7 @@ typedef struct {
   int blk_ctas_per_sm;
   int general_update;
   int chain_warps;
+  int long_chain_split;
 } negf_opts;
 
 /* Create / destroy a context on one GPU.  opts may be NULL (defaults: device 0, own

@@ -129,7 +129,8 @@ int check_ready(Ctx* c, Dev* d) {
 // reset, sweeps, second stage), so it can be captured in a CUDA graph and replayed.
 void free_plan_bufs(Ctx* c, PlanBufs& b) {
   for (DBuf* x : {&b.views, &b.items, &b.order, &b.counter, &b.partial, &b.tpart, &b.stage, &b.reduce, &b.status,
-                  &b.resid, &b.order2, &b.growth, &b.prep, &b.hu, &b.gen, &b.genjobs, &b.genstat})
+                  &b.resid, &b.order2, &b.growth, &b.prep, &b.hu, &b.gen, &b.genjobs, &b.genstat,
+                  &b.segitems, &b.recitem, &b.segrec})
     c->arena.release(*x);
 }
 
@@ -412,6 +413,35 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
   P.n_items = n_items;
   P.tpos = tpos;
 
+  // FP64 1 x 1 items of long channels with few energies are swept split along the channel
+  // (sweep_seg.cu).  The rule looks at the device alone, never at the rest of the batch.
+  std::vector<char> is_seg(n_items, 0);
+  if (c->opts.long_chain_split >= 0) {
+    for (int di = 0; di < nd; ++di) {
+      if (devs[di]->block != 1) continue;
+      int n64 = 0;
+      for (int i = P.it0[di]; i < P.it0[di + 1]; ++i) n64 += items[i].pad == 0;
+      const bool split = c->opts.long_chain_split == 1 || (P.views[di].L >= SEG_MIN_L && n64 <= SEG_MAX_ITEMS);
+      if (!split) continue;
+      for (int i = P.it0[di]; i < P.it0[di + 1]; ++i)
+        if (items[i].pad == 0) {
+          is_seg[i] = 1;
+          SegItem S;
+          S.item = i;
+          S.n_seg = (P.views[di].L + SEG_LEN - 1) / SEG_LEN;
+          S.rec0 = 0;
+          S.stage = 0;
+          P.seg.push_back(S);
+        }
+    }
+    // the per-warp staging of the 1 x 1 groups is sized by the items they still run
+    if (!P.seg.empty()) {
+      Lmax[0] = 0;
+      for (int i = 0; i < n_items; ++i)
+        if (!is_seg[i] && (items[i].pad == 0 || items[i].pad == 5)) Lmax[0] = std::max(Lmax[0], P.views[items[i].dev].L);
+    }
+  }
+
   // band-edge flags of the mixed path: |E - U_lead - e| < window for an edge e of a lead
   // mode, e in {+-|sqrt(a1) - sqrt(a2)|, +-(sqrt(a1) + sqrt(a2))}
   if (P.prec == NEGF_PREC_MIXED) {
@@ -443,7 +473,8 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
 
   // schedule order per group: longest first
   std::vector<int> order[NGROUPS];
-  for (int i = 0; i < n_items; ++i) order[items[i].pad].push_back(i);
+  for (int i = 0; i < n_items; ++i)
+    if (!is_seg[i]) order[items[i].pad].push_back(i);
   for (int g = 0; g < NGROUPS; ++g) {
     auto cost = [&](int i) {
       const Dev* d = devs[items[i].dev];
@@ -551,6 +582,46 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       }
     }
 
+  // split items in waves: consecutive items whose staging fits cap (an item alone may not);
+  // returns the largest staging of a wave and sets the records of the largest wave
+  long long seg_recs = 0;
+  auto seg_waves = [&](long long cap) -> long long {
+    P.seg_waves.clear();
+    seg_recs = 0;
+    long long st = 0, rec = 0, r0 = 0, worst = 0;
+    int i0 = 0;
+    for (int j = 0; j < (int)P.seg.size(); ++j) {
+      SegItem& S = P.seg[j];
+      const WorkItem& W = items[S.item];
+      const long long b = (long long)seg_stage_bytes(P.views[W.dev].L, W.kind);
+      if (j > i0 && st + b > cap) {
+        P.seg_waves.push_back({i0, j - i0, r0, rec});
+        seg_recs = std::max(seg_recs, rec);
+        r0 += rec;
+        i0 = j;
+        st = 0;
+        rec = 0;
+      }
+      S.rec0 = rec;
+      S.stage = st;
+      st += b;
+      rec += S.n_seg;
+      worst = std::max(worst, st);
+    }
+    if (!P.seg.empty()) {
+      P.seg_waves.push_back({i0, (int)P.seg.size() - i0, r0, rec});
+      seg_recs = std::max(seg_recs, rec);
+    }
+    return worst;
+  };
+  constexpr long long SEG_WAVE_BYTES = 4LL << 30;
+  stage_bytes = std::max(stage_bytes, seg_waves(SEG_WAVE_BYTES));
+  long long seg_rec_total = 0;
+  for (const SegItem& S : P.seg) seg_rec_total += S.n_seg;
+  const size_t segrec_bytes = (size_t)std::max<long long>(seg_recs * SEG_FIELDS * 32 * 8, 16);
+  const size_t segitem_bytes = std::max<size_t>(sizeof(SegItem) * P.seg.size(), 16);
+  const size_t recitem_bytes = (size_t)std::max<long long>(seg_rec_total * 4, 16);
+
   // layer diagonals of the 1 x 1 chains, formed once per launch by prep_kernel
   long long hu_elems = 0;
   int n_prep = 0, prep_L = 0;
@@ -574,7 +645,8 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
                       extra(B.order, sizeof(int) * n_items) + extra(B.partial, sizeof(double) * std::max<long long>(part, 1)) +
                       extra(B.tpart, sizeof(double) * std::max<long long>(tpos, 1)) + extra(B.reduce, sizeof(ReduceDev) * nd) +
                       extra(B.counter, sizeof(int) * 16) + extra(B.status, sizeof(int)) + extra(B.hu, hu_bytes) +
-                      extra(B.prep, prep_bytes);
+                      extra(B.prep, prep_bytes) + extra(B.segitems, segitem_bytes) + extra(B.recitem, recitem_bytes) +
+                      extra(B.segrec, segrec_bytes);
     if (P.prec != NEGF_PREC_FP64)
       other += extra(B.resid, sizeof(double) * tpos) + extra(B.growth, sizeof(double) * tpos) + extra(B.order2, sizeof(int) * n_items);
     for (int di = 0; di < nd; ++di) {
@@ -596,6 +668,11 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
         P.grid[g] = (int)std::min<long long>(P.grid[g], fit);
         stage_bytes = std::max(stage_bytes, per * P.grid[g]);
       }
+      if (!P.seg.empty()) {
+        const long long sw = seg_waves(cap);
+        if (sw > cap) return set_err(c, NEGF_ENOMEM, "budget too small for the staging of one split chain");
+        stage_bytes = std::max(stage_bytes, sw);
+      }
     }
   }
   if (!ensure(c, B.views, sizeof(DeviceView) * nd) || !ensure(c, B.items, sizeof(WorkItem) * n_items) ||
@@ -605,6 +682,8 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       !ensure(c, B.stage, (size_t)std::max<long long>(stage_bytes, 16)) ||
       !ensure(c, B.reduce, sizeof(ReduceDev) * nd) || !ensure(c, B.status, sizeof(int)) ||
       !ensure(c, B.hu, hu_bytes) || !ensure(c, B.prep, prep_bytes) ||
+      (!P.seg.empty() && (!ensure(c, B.segitems, segitem_bytes) || !ensure(c, B.recitem, recitem_bytes) ||
+                          !ensure(c, B.segrec, segrec_bytes))) ||
       (P.prec != NEGF_PREC_FP64 && (!ensure(c, B.resid, sizeof(double) * std::max<long long>(tpos, 1)) ||
                                     !ensure(c, B.growth, sizeof(double) * std::max<long long>(tpos, 1)) ||
                                     !ensure(c, B.order2, sizeof(int) * n_items))))
@@ -715,9 +794,22 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       (n_prep && cudaMemcpy(B.prep.p, prep.data(), sizeof(PrepDesc) * n_prep, cudaMemcpyHostToDevice)) ||
       cudaMemcpy(B.views.p, P.views.data(), sizeof(DeviceView) * nd, cudaMemcpyHostToDevice) ||
       cudaMemcpy(B.items.p, items.data(), sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice) ||
-      cudaMemcpy(B.order.p, order_all.data(), sizeof(int) * n_items, cudaMemcpyHostToDevice) ||
+      (!order_all.empty() &&   // split items have no place in the schedule of the sweep groups
+       cudaMemcpy(B.order.p, order_all.data(), sizeof(int) * order_all.size(), cudaMemcpyHostToDevice)) ||
       cudaMemcpy(B.reduce.p, rd.data(), sizeof(ReduceDev) * nd, cudaMemcpyHostToDevice))
     return set_err(c, NEGF_ECUDA, "upload of the launch plan failed");
+  if (!P.seg.empty()) {
+    // owner of every record, relative to its wave's first item
+    std::vector<int> owner;
+    owner.reserve((size_t)seg_rec_total);
+    for (const Plan::SegWave& wv : P.seg_waves)
+      for (int j = 0; j < wv.ni; ++j)
+        owner.insert(owner.end(), (size_t)P.seg[wv.i0 + j].n_seg, j);
+    if ((long long)owner.size() != seg_rec_total ||
+        cudaMemcpy(B.segitems.p, P.seg.data(), sizeof(SegItem) * P.seg.size(), cudaMemcpyHostToDevice) ||
+        cudaMemcpy(B.recitem.p, owner.data(), sizeof(int) * owner.size(), cudaMemcpyHostToDevice))
+      return set_err(c, NEGF_ECUDA, "upload of the split-chain plan failed");
+  }
   if (!jobs.empty()) {
     int max_e = 1, m_max = 1;
     for (const GenLeadJob& j : jobs) {
@@ -852,6 +944,23 @@ int launch_plan(Ctx* c, Plan& P) {
     double* growth = group_f32(g) ? (double*)B.growth.p : nullptr;
     int rc = launch_group(c, P, g, (const int*)B.order.p + P.ooff[g], P.ncls[g], P.grid[g], resid, growth);
     if (rc) return rc;
+  }
+  for (const Plan::SegWave& wv : P.seg_waves) {
+    SegArgs a;
+    a.devs = (const DeviceView*)B.views.p;
+    a.items = (const WorkItem*)B.items.p;
+    a.segs = (const SegItem*)B.segitems.p + wv.i0;
+    a.rec_item = (const int*)B.recitem.p + wv.r0;
+    a.n_rec = wv.nr;
+    a.n_segitems = wv.ni;
+    a.rec = (double*)B.segrec.p;
+    a.stage = (unsigned char*)B.stage.p;
+    a.partial = (double*)B.partial.p;
+    a.Tpart = (double*)B.tpart.p;
+    a.ring_cap = P.ring_cap;
+    a.cap_ring = P.cap_ring;
+    if (launch_seg(a, s)) return set_err(c, NEGF_ECUDA, "split-chain sweep launch failed");
+    c->launches += 5;
   }
   if (P.prec == NEGF_PREC_MIXED) {
     if (cap != cudaStreamCaptureStatusNone) return set_err(c, NEGF_EINVAL, "mixed precision cannot be captured");

@@ -68,6 +68,7 @@ struct PlanBufs {
   DBuf views, items, order, counter, partial, tpart, stage, reduce, status, resid, order2, growth;
   DBuf prep, hu;   // layer diagonals of the 1 x 1 chains (descriptors, values)
   DBuf gen, genjobs, genstat;   // general leads: per-energy Sigma and Gamma factors, jobs, status
+  DBuf segitems, recitem, segrec;   // chains split along the channel: items, record owners, records
 };
 
 struct ScSession;
@@ -185,6 +186,14 @@ struct Plan {
   int n_prep = 0, prep_L = 0;             // prep_kernel descriptors and longest chain
   double* ring_cap = nullptr;             // per-energy contributions at ring cap_ring (1 x 1, 2 x 2)
   int cap_ring = -1;
+  // FP64 1 x 1 items swept split along the channel (sweep_seg.cu), run in waves whose staging
+  // fits the stage buffer
+  struct SegWave {
+    int i0, ni;          // range of SegItems
+    long long r0, nr;    // range of records
+  };
+  std::vector<SegItem> seg;
+  std::vector<SegWave> seg_waves;
 };
 int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOverride>* ov, int chain_only,
                Plan& P, PlanBufs* bufs = nullptr);

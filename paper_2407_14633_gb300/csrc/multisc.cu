@@ -239,6 +239,7 @@ int negf_sc_solve_multi(negf_ctx* c, const int* devs, int C, const negf_bias* bi
   // gather, Broyden (an uncaptured iteration counts the plan's own launches in launch_plan)
   uint64_t per_iter = 4 + (plan.n_prep > 0 ? 1 : 0);
   for (int g = 0; g < NGROUPS; ++g) per_iter += (plan.ncls[g] > 0);
+  per_iter += 5 * plan.seg_waves.size();
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
     const uint64_t l0 = c->launches;
     const bool ok = iteration() == NEGF_OK;

@@ -51,6 +51,7 @@ static void capture_iteration(Ctx* c, ScSession* s) {
   // Poisson, the sweep groups, the layer-diagonal prep of 1 x 1 chains, second stage, Broyden
   s->kernels_per_iter = 3 + (s->plan.n_prep > 0 ? 1 : 0);
   for (int g = 0; g < NGROUPS; ++g) s->kernels_per_iter += (s->plan.ncls[g] > 0);
+  s->kernels_per_iter += 5 * s->plan.seg_waves.size();
   const ScDev* dsc = (const ScDev*)s->sc.p;
   if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
     const uint64_t l0 = c->launches;

@@ -459,17 +459,30 @@ def paper_scaling(reps=2):
             ms, k = ctx.kernel_time()
         out["table1"].append({"N": N, "negf_ms": wall * 1e3, "sweep_ms": ms / max(k, 1),
                               "paper_s": ps, "paper_a100s": ng})
+    # Table 2 twice: the sweep split along the channel (the default for these shapes) and the
+    # thread-per-lane sweep of whole chains
     t2 = w["table2"]
     N = t2["N"]
     for modes, ps in zip(t2["modes"], t2["paper_s"]):
-        with negf.Context() as ctx:
-            dev = ctx.device_create(N, block=1, rings_per_block=1, n_chains=len(modes))
-            ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], list(modes), 0.0, 0.0)
-            ctx.set_potential(dev, np.zeros(N))
-            ctx.set_grid_spec(dev, 0.0, 0.0, w["kT"], w["eta"], -3.0 * abs(w["t"]) - 1.0, 0, t2["n_cont"])
-            ctx.compute([dev])
-            t0 = time.perf_counter()
-            ctx.compute([dev])
-            wall = time.perf_counter() - t0
-        out["table2"].append({"modes": len(modes), "negf_ms": wall * 1e3, "paper_s": ps})
+        row = {"modes": len(modes), "paper_s": ps}
+        n_ref = None
+        for key, split in (("negf_ms", 0), ("unsplit_ms", -1)):
+            with negf.Context(long_chain_split=split) as ctx:
+                dev = ctx.device_create(N, block=1, rings_per_block=1, n_chains=len(modes))
+                ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], list(modes), 0.0, 0.0)
+                ctx.set_potential(dev, np.zeros(N))
+                ctx.set_grid_spec(dev, 0.0, 0.0, w["kT"], w["eta"], -3.0 * abs(w["t"]) - 1.0, 0, t2["n_cont"])
+                ctx.compute([dev])
+                ctx.profile(True)
+                ctx.kernel_time()
+                t0 = time.perf_counter()
+                r = ctx.compute([dev])[0]
+                row[key] = (time.perf_counter() - t0) * 1e3
+                ms, k = ctx.kernel_time()
+                row[key.replace("negf", "sweep").replace("unsplit", "unsplit_sweep")] = ms / max(k, 1)
+                if n_ref is None:
+                    n_ref = r["n"]
+                else:
+                    row["max_rel_diff_n"] = float(np.max(np.abs(r["n"] - n_ref)) / np.max(np.abs(n_ref)))
+        out["table2"].append(row)
     return out
