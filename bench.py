@@ -372,7 +372,9 @@ def run_profile_small(args):
     contour energies, so the same lanes and waves as the bench workload at 1/8 of its length),
     complex128.  rs17_c64: the same with the complex64 sweep.  mode: eight (17,0) mode-space
     devices, modes 6 and 5, N = 1000, 4032 + 64 energies each (the thread-per-lane 1 x 1 sweep
-    of the batched and serving workloads), complex128."""
+    of the batched and serving workloads), complex128.  long: the paper's Table 2 shape at a
+    quarter of its length, one (17,0) mode-space device of N = 131,072 rings, modes 6 and 5,
+    90 contour nodes and no real-axis lanes (the sweep split along the channel), complex128."""
     import torch
     from paper_2407_14633_gb300 import negf, synth
     stream = torch.cuda.Stream()
@@ -381,7 +383,15 @@ def run_profile_small(args):
     ctx = negf.Context(device=0, stream=stream.cuda_stream, blk_warps=args.blk_warps,
                        blk_ctas_per_sm=args.blk_ctas, precision=prec)
     n_dev = 1
-    if args.profile_case == "mode":
+    if args.profile_case == "long":
+        ps = synth.paper_scaling()
+        N, n_cont = 131072, ps["table2"]["n_cont"]
+        w = dict(N=N, n_real=0, n_cont=n_cont, t=ps["t"], U=np.zeros(N), U_S=0.0, U_D=0.0, mu_S=0.0, mu_D=0.0,
+                 kT=ps["kT"], eta=ps["eta"], E_B=-3.0 * abs(ps["t"]) - 1.0)
+        devs = [ctx.device_create(N, block=1, rings_per_block=1, n_chains=2)]
+        ctx.build_cnt_modespace(devs[0], ps["n_tube"], w["t"], [6, 5], 0.0, 0.0)
+        flops = None
+    elif args.profile_case == "mode":
         N, n_real, n_cont, n_dev = 1000, 4032, 64, 8
         w = synth.realspace_17(N=N, n_real=n_real, n_cont=n_cont)
         devs = [ctx.device_create(N, block=1, rings_per_block=1, n_chains=2) for _ in range(n_dev)]
@@ -408,7 +418,7 @@ def run_profile_small(args):
     if flops:
         line["tflops"] = flops / (ms / k * 1e-3) / 1e12
     else:
-        updates = n_dev * w["N"] * 2 * (w["n_real"] + w["n_cont"])
+        updates = n_dev * w["N"] * 2 * (w["n_real"] + w["n_cont"])   # two modes per device
         line["ring_energy_mode_updates_per_s"] = updates / (ms / k * 1e-3)
     print(json.dumps(line))
     ctx.close()
@@ -431,7 +441,7 @@ def main():
                     help="reduced case of the block sweep for ncu captures")
     ap.add_argument("--blk-warps", type=int, default=1,
                     help="CTA width of the block sweep in --profile-small (no tuning launches)")
-    ap.add_argument("--profile-case", default="rs17", choices=["rs17", "rs17_c64", "mode"],
+    ap.add_argument("--profile-case", default="rs17", choices=["rs17", "rs17_c64", "mode", "long"],
                     help="which reduced case --profile-small runs")
     ap.add_argument("--blk-ctas", type=int, default=0,
                     help="cap on resident CTAs per SM of the block sweep in --profile-small (0: no cap)")

@@ -265,7 +265,8 @@ struct ReduceDev {
   double* T;
   double* I;
 };
-int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s);
+// second stage: one CTA column per device, ceil(max_rings / 256) CTAs (at most 1024) along its rings
+int launch_reduce(const ReduceDev* devs, int n_devs, int max_rings, cudaStream_t s);
 
 // Zero-bias conductance of one device (Eq. zeroBiasG): G = g_s (e^2/h) sum_k w_k T_k (-df/dE)(E_k - mu).
 struct CondDev {

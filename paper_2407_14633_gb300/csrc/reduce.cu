@@ -14,11 +14,14 @@ namespace negf {
 // e^2/h in A/V from the exact SI 2019 elementary charge and Planck constant
 __constant__ double kE2H = 1.602176634e-19 * 1.602176634e-19 / 6.62607015e-34;
 
+// Grid: one column of CTAs per device (blockIdx.x), its rings spread over blockIdx.y.  Each
+// ring's sum runs over the device's items in order in one thread, whichever thread that is;
+// the first CTA of a column also reduces T(E) and the current.
 __global__ void __launch_bounds__(256) reduce_kernel(const ReduceDev* devs) {
   const ReduceDev& R = devs[blockIdx.x];
   __shared__ double sh[256];
   // ring sums: real-axis items and contour items separately
-  for (int r = threadIdx.x; r < R.n_rings; r += blockDim.x) {
+  for (int r = blockIdx.y * blockDim.x + threadIdx.x; r < R.n_rings; r += gridDim.y * blockDim.x) {
     double sr = 0.0, sc = 0.0;
     for (int it = R.it0; it < R.it1; ++it) {
       const WorkItem& W = R.items[it];
@@ -32,6 +35,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReduceDev* devs) {
     if (R.n_real_part) R.n_real_part[r] = sr;
     if (R.n_cont) R.n_cont[r] = sc;
   }
+  if (blockIdx.y != 0) return;
   // T(E) and the current
   double acc = 0.0;
   for (int k = threadIdx.x; k < R.n_real; k += blockDim.x) {
@@ -49,8 +53,9 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReduceDev* devs) {
   if (threadIdx.x == 0 && R.I) *R.I = 2.0 * kE2H * sh[0];
 }
 
-int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s) {
-  reduce_kernel<<<n_devs, 256, 0, s>>>(devs);
+int launch_reduce(const ReduceDev* devs, int n_devs, int max_rings, cudaStream_t s) {
+  const int cols = std::max(1, std::min((max_rings + 255) / 256, 1024));
+  reduce_kernel<<<dim3(n_devs, cols), 256, 0, s>>>(devs);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

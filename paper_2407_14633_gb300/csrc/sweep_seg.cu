@@ -169,16 +169,23 @@ __global__ void __launch_bounds__(32) seg_fscan_kernel(SegArgs a) {
   if (i >= a.n_segitems) return;
   const SegItem S = a.segs[i];
   cd g = mk(0.0, 0.0);
-#pragma unroll 4
+  // the next segment's map is loaded one step ahead (the stores of this step would otherwise
+  // order it behind them)
+  double m[8], nx[8];
+  const double* r0 = rec_ptr(a, S.rec0);
+#pragma unroll
+  for (int f = 0; f < 8; ++f) m[f] = r0[(F_MAP + f) * 32 + lane];
   for (int s = 0; s < S.n_seg; ++s) {
     double* rp = rec_ptr(a, S.rec0 + s);
-    const cd ma = mk(rp[(F_MAP + 0) * 32 + lane], rp[(F_MAP + 1) * 32 + lane]);
-    const cd mb = mk(rp[(F_MAP + 2) * 32 + lane], rp[(F_MAP + 3) * 32 + lane]);
-    const cd mc = mk(rp[(F_MAP + 4) * 32 + lane], rp[(F_MAP + 5) * 32 + lane]);
-    const cd md = mk(rp[(F_MAP + 6) * 32 + lane], rp[(F_MAP + 7) * 32 + lane]);
-    g = cdiv(cmac(mb, ma, g), cmac(md, mc, g));
+    if (s + 1 < S.n_seg) {
+#pragma unroll
+      for (int f = 0; f < 8; ++f) nx[f] = rp[SEG_FIELDS * 32 + (F_MAP + f) * 32 + lane];
+    }
+    g = cdiv(cmac(mk(m[2], m[3]), mk(m[0], m[1]), g), cmac(mk(m[6], m[7]), mk(m[4], m[5]), g));
     rp[(F_GEND + 0) * 32 + lane] = g.re;
     rp[(F_GEND + 1) * 32 + lane] = g.im;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) m[f] = nx[f];
   }
 }
 
@@ -252,23 +259,33 @@ __global__ void __launch_bounds__(32) seg_bscan_kernel(SegArgs a) {
   const SegItem S = a.segs[i];
   cd G = mk(0.0, 0.0);
   double c = 1.0;
-#pragma unroll 4
+  // fields F_A .. F_CP of the current segment, the next one's loaded one step ahead
+  double m[6], nx[6];
+  const double* rl = rec_ptr(a, S.rec0 + S.n_seg - 1);
+#pragma unroll
+  for (int f = 0; f < 6; ++f) m[f] = rl[(F_A + f) * 32 + lane];
   for (int s = S.n_seg - 1; s >= 0; --s) {
     double* rp = rec_ptr(a, S.rec0 + s);
+    if (s > 0) {
+#pragma unroll
+      for (int f = 0; f < 6; ++f) nx[f] = rp[-SEG_FIELDS * 32 + (F_A + f) * 32 + lane];
+    }
     rp[(F_GIN + 0) * 32 + lane] = G.re;
     rp[(F_GIN + 1) * 32 + lane] = G.im;
     rp[F_CIN * 32 + lane] = c;
-    const cd A = mk(rp[(F_A + 0) * 32 + lane], rp[(F_A + 1) * 32 + lane]);
-    const cd B = mk(rp[(F_B + 0) * 32 + lane], rp[(F_B + 1) * 32 + lane]);
-    G = cmac(A, B, G);
-    c = rp[F_CP * 32 + lane] * c;
+    G = cmac(mk(m[0], m[1]), mk(m[2], m[3]), G);
+    c = m[F_CP - F_A] * c;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) m[f] = nx[f];
   }
   double qv = rec_ptr(a, S.rec0)[F_Q0 * 32 + lane];
-#pragma unroll 4
+  double qp = rec_ptr(a, S.rec0)[F_QP * 32 + lane], qn = 0.0;
   for (int s = 0; s < S.n_seg; ++s) {
     double* rp = rec_ptr(a, S.rec0 + s);
+    if (s + 1 < S.n_seg) qn = rp[SEG_FIELDS * 32 + F_QP * 32 + lane];
     rp[F_QIN * 32 + lane] = qv;
-    qv = rp[F_QP * 32 + lane] * qv;
+    qv = qp * qv;
+    qp = qn;
   }
 }
 
@@ -339,7 +356,8 @@ size_t seg_stage_bytes(int L, int kind) { return (size_t)L * (kind == 0 ? 3 : 2)
 
 int launch_seg(const SegArgs& a, cudaStream_t s) {
   if (a.n_rec <= 0 || a.n_segitems <= 0) return 0;
-  constexpr int WPB = 4;
+  // one warp per CTA: the records spread over the SMs within one CTA of each other
+  constexpr int WPB = 1;
   const long long grid = (a.n_rec + WPB - 1) / WPB;
   if (grid > 0x7fffffffLL) return -1;
   const size_t smem = (size_t)WPB * 32 * 33 * sizeof(double);
