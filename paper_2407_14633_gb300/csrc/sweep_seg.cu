@@ -18,7 +18,8 @@
 // Five launches per wave of items: (1) segment maps, (2) scan of the forward maps, (3) the
 // forward recursion re-run from the scanned entry value (staging gL and the source weight,
 // composing the backward maps), (4) scan of the backward maps and products, (5) the backward
-// recursion with the per-ring quadrature reduction of the thread-per-lane sweep.  Segments
+// recursion with the per-ring quadrature reduction of the thread-per-lane sweep.  The scans
+// are two-level: maps composed per chunk of segments, chained, then walked per chunk.  Segments
 // are fixed per device (SEG_LEN layers), so every result is the same in any batch.
 #include "common.cuh"
 #include "lead.cuh"
@@ -161,31 +162,69 @@ __global__ void __launch_bounds__(128) seg_map_kernel(SegArgs a) {
   rp[(F_MAP + 7) * 32 + lane] = md.im;
 }
 
-// (2) gL leaving each segment: g <- (a g + b) / (c g + d), segment by segment; one thread per
-// (item, lane)
-__global__ void __launch_bounds__(32) seg_fscan_kernel(SegArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x;
-  if (i >= a.n_segitems) return;
-  const SegItem S = a.segs[i];
-  cd g = mk(0.0, 0.0);
-  // the next segment's map is loaded one step ahead (the stores of this step would otherwise
-  // order it behind them)
-  double m[8], nx[8];
-  const double* r0 = rec_ptr(a, S.rec0);
-#pragma unroll
-  for (int f = 0; f < 8; ++f) m[f] = r0[(F_MAP + f) * 32 + lane];
-  for (int s = 0; s < S.n_seg; ++s) {
-    double* rp = rec_ptr(a, S.rec0 + s);
-    if (s + 1 < S.n_seg) {
-#pragma unroll
-      for (int f = 0; f < 8; ++f) nx[f] = rp[SEG_FIELDS * 32 + (F_MAP + f) * 32 + lane];
+// Scans over an item's segments, one CTA of SCAN_WARPS warps per item (lane = energy): each
+// warp composes the maps of one chunk of consecutive segments, warp 0 chains the chunks, then
+// each warp walks its own segments from its chunk's entry value.
+constexpr int SCAN_WARPS = 16;
+
+__device__ __forceinline__ void chunk_range(int n, int w, int& s0, int& s1) {
+  const int per = (n + SCAN_WARPS - 1) / SCAN_WARPS;
+  s0 = min(n, w * per);
+  s1 = min(n, s0 + per);
+}
+
+// (2) gL leaving each segment: g <- (a g + b) / (c g + d) over the segments in order
+__global__ void __launch_bounds__(32 * SCAN_WARPS) seg_fscan_kernel(SegArgs a) {
+  __shared__ double chm[SCAN_WARPS][8][32];   // chunk maps
+  __shared__ double ent[SCAN_WARPS][2][32];   // gL entering each chunk
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const SegItem S = a.segs[blockIdx.x];
+  int s0, s1;
+  chunk_range(S.n_seg, w, s0, s1);
+  // chunk product M = M_{s1-1} ... M_{s0}
+  cd A = mk(1.0, 0.0), B = mk(0.0, 0.0), C = mk(0.0, 0.0), D = mk(1.0, 0.0);
+  for (int s = s0; s < s1; ++s) {
+    const double* rp = rec_ptr(a, S.rec0 + s);
+    const cd ma = mk(rp[(F_MAP + 0) * 32 + lane], rp[(F_MAP + 1) * 32 + lane]);
+    const cd mb = mk(rp[(F_MAP + 2) * 32 + lane], rp[(F_MAP + 3) * 32 + lane]);
+    const cd mc = mk(rp[(F_MAP + 4) * 32 + lane], rp[(F_MAP + 5) * 32 + lane]);
+    const cd md = mk(rp[(F_MAP + 6) * 32 + lane], rp[(F_MAP + 7) * 32 + lane]);
+    const cd nA = cmac(ma * A, mb, C), nB = cmac(ma * B, mb, D);
+    const cd nC = cmac(mc * A, md, C), nD = cmac(mc * B, md, D);
+    A = nA;
+    B = nB;
+    C = nC;
+    D = nD;
+    renorm(A, B, C, D);
+  }
+  chm[w][0][lane] = A.re;
+  chm[w][1][lane] = A.im;
+  chm[w][2][lane] = B.re;
+  chm[w][3][lane] = B.im;
+  chm[w][4][lane] = C.re;
+  chm[w][5][lane] = C.im;
+  chm[w][6][lane] = D.re;
+  chm[w][7][lane] = D.im;
+  __syncthreads();
+  if (w == 0) {
+    cd g = mk(0.0, 0.0);
+    for (int k = 0; k < SCAN_WARPS; ++k) {
+      ent[k][0][lane] = g.re;
+      ent[k][1][lane] = g.im;
+      g = cdiv(cmac(mk(chm[k][2][lane], chm[k][3][lane]), mk(chm[k][0][lane], chm[k][1][lane]), g),
+               cmac(mk(chm[k][6][lane], chm[k][7][lane]), mk(chm[k][4][lane], chm[k][5][lane]), g));
     }
-    g = cdiv(cmac(mk(m[2], m[3]), mk(m[0], m[1]), g), cmac(mk(m[6], m[7]), mk(m[4], m[5]), g));
+  }
+  __syncthreads();
+  cd g = mk(ent[w][0][lane], ent[w][1][lane]);
+  for (int s = s0; s < s1; ++s) {
+    double* rp = rec_ptr(a, S.rec0 + s);
+    g = cdiv(cmac(mk(rp[(F_MAP + 2) * 32 + lane], rp[(F_MAP + 3) * 32 + lane]),
+                  mk(rp[(F_MAP + 0) * 32 + lane], rp[(F_MAP + 1) * 32 + lane]), g),
+             cmac(mk(rp[(F_MAP + 6) * 32 + lane], rp[(F_MAP + 7) * 32 + lane]),
+                  mk(rp[(F_MAP + 4) * 32 + lane], rp[(F_MAP + 5) * 32 + lane]), g));
     rp[(F_GEND + 0) * 32 + lane] = g.re;
     rp[(F_GEND + 1) * 32 + lane] = g.im;
-#pragma unroll
-    for (int f = 0; f < 8; ++f) m[f] = nx[f];
   }
 }
 
@@ -251,41 +290,64 @@ __global__ void __launch_bounds__(128) seg_rerun_kernel(SegArgs a) {
 }
 
 // (4) entry values of the backward re-run: G and the drain column from the right, the source
-// weight from the left
-__global__ void __launch_bounds__(32) seg_bscan_kernel(SegArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x;
-  if (i >= a.n_segitems) return;
-  const SegItem S = a.segs[i];
-  cd G = mk(0.0, 0.0);
-  double c = 1.0;
-  // fields F_A .. F_CP of the current segment, the next one's loaded one step ahead
-  double m[6], nx[6];
-  const double* rl = rec_ptr(a, S.rec0 + S.n_seg - 1);
-#pragma unroll
-  for (int f = 0; f < 6; ++f) m[f] = rl[(F_A + f) * 32 + lane];
-  for (int s = S.n_seg - 1; s >= 0; --s) {
-    double* rp = rec_ptr(a, S.rec0 + s);
-    if (s > 0) {
-#pragma unroll
-      for (int f = 0; f < 6; ++f) nx[f] = rp[-SEG_FIELDS * 32 + (F_A + f) * 32 + lane];
+// weight from the left (chunks as in the forward scan)
+__global__ void __launch_bounds__(32 * SCAN_WARPS) seg_bscan_kernel(SegArgs a) {
+  __shared__ double chm[SCAN_WARPS][6][32];   // chunk maps: A, B, CP, QP
+  __shared__ double ent[SCAN_WARPS][4][32];   // G and c at each chunk's right end, q at its left end
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const SegItem S = a.segs[blockIdx.x];
+  int s0, s1;
+  chunk_range(S.n_seg, w, s0, s1);
+  // chunk composition: G_{left} = A + B G_{right}; products of the drain and source factors
+  cd A = mk(0.0, 0.0), B = mk(1.0, 0.0);
+  double cp = 1.0, qp = 1.0;
+  for (int s = s0; s < s1; ++s) {
+    const double* rp = rec_ptr(a, S.rec0 + s);
+    A = cmac(A, B, mk(rp[(F_A + 0) * 32 + lane], rp[(F_A + 1) * 32 + lane]));
+    B = B * mk(rp[(F_B + 0) * 32 + lane], rp[(F_B + 1) * 32 + lane]);
+    cp = cp * rp[F_CP * 32 + lane];
+    qp = rp[F_QP * 32 + lane] * qp;
+  }
+  chm[w][0][lane] = A.re;
+  chm[w][1][lane] = A.im;
+  chm[w][2][lane] = B.re;
+  chm[w][3][lane] = B.im;
+  chm[w][4][lane] = cp;
+  chm[w][5][lane] = qp;
+  __syncthreads();
+  if (w == 0) {
+    cd G = mk(0.0, 0.0);
+    double c = 1.0;
+    for (int k = SCAN_WARPS - 1; k >= 0; --k) {
+      ent[k][0][lane] = G.re;
+      ent[k][1][lane] = G.im;
+      ent[k][2][lane] = c;
+      G = cmac(mk(chm[k][0][lane], chm[k][1][lane]), mk(chm[k][2][lane], chm[k][3][lane]), G);
+      c = chm[k][4][lane] * c;
     }
+    double q = rec_ptr(a, S.rec0)[F_Q0 * 32 + lane];
+    for (int k = 0; k < SCAN_WARPS; ++k) {
+      ent[k][3][lane] = q;
+      q = chm[k][5][lane] * q;
+    }
+  }
+  __syncthreads();
+  cd G = mk(ent[w][0][lane], ent[w][1][lane]);
+  double c = ent[w][2][lane];
+  for (int s = s1 - 1; s >= s0; --s) {
+    double* rp = rec_ptr(a, S.rec0 + s);
     rp[(F_GIN + 0) * 32 + lane] = G.re;
     rp[(F_GIN + 1) * 32 + lane] = G.im;
     rp[F_CIN * 32 + lane] = c;
-    G = cmac(mk(m[0], m[1]), mk(m[2], m[3]), G);
-    c = m[F_CP - F_A] * c;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) m[f] = nx[f];
+    G = cmac(mk(rp[(F_A + 0) * 32 + lane], rp[(F_A + 1) * 32 + lane]),
+             mk(rp[(F_B + 0) * 32 + lane], rp[(F_B + 1) * 32 + lane]), G);
+    c = rp[F_CP * 32 + lane] * c;
   }
-  double qv = rec_ptr(a, S.rec0)[F_Q0 * 32 + lane];
-  double qp = rec_ptr(a, S.rec0)[F_QP * 32 + lane], qn = 0.0;
-  for (int s = 0; s < S.n_seg; ++s) {
+  double q = ent[w][3][lane];
+  for (int s = s0; s < s1; ++s) {
     double* rp = rec_ptr(a, S.rec0 + s);
-    if (s + 1 < S.n_seg) qn = rp[SEG_FIELDS * 32 + F_QP * 32 + lane];
-    rp[F_QIN * 32 + lane] = qv;
-    qv = qp * qv;
-    qp = qn;
+    rp[F_QIN * 32 + lane] = q;
+    q = rp[F_QP * 32 + lane] * q;
   }
 }
 
@@ -362,9 +424,9 @@ int launch_seg(const SegArgs& a, cudaStream_t s) {
   if (grid > 0x7fffffffLL) return -1;
   const size_t smem = (size_t)WPB * 32 * 33 * sizeof(double);
   seg_map_kernel<<<(unsigned)grid, 32 * WPB, 0, s>>>(a);
-  seg_fscan_kernel<<<a.n_segitems, 32, 0, s>>>(a);
+  seg_fscan_kernel<<<a.n_segitems, 32 * SCAN_WARPS, 0, s>>>(a);
   seg_rerun_kernel<<<(unsigned)grid, 32 * WPB, 0, s>>>(a);
-  seg_bscan_kernel<<<a.n_segitems, 32, 0, s>>>(a);
+  seg_bscan_kernel<<<a.n_segitems, 32 * SCAN_WARPS, 0, s>>>(a);
   seg_back_kernel<<<(unsigned)grid, 32 * WPB, smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
