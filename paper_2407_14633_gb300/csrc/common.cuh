@@ -218,37 +218,6 @@ int sweep_blk_occupancy_t(bool fp32, int warps, int b, int m);
 int sweep_chain_occupancy(int cls, int threads, size_t smem);
 int sweep_chain_occupancy_t(bool fp32, int cls, int threads, size_t smem);
 
-// Sweep of a 1 x 1 chain split along the channel (sweep_seg.cu): segments of SEG_LEN layers, one
-// warp per (item, segment).  Used for FP64 items of devices with at least SEG_MIN_L layers and
-// at most SEG_MAX_ITEMS such items of their own.
-constexpr int SEG_LEN = 512;
-constexpr int SEG_MIN_L = 16384;
-constexpr int SEG_MAX_ITEMS = 128;
-constexpr int SEG_FIELDS = 21;     // doubles per lane of a segment record
-struct SegItem {
-  int item;        // index into the plan's WorkItem array
-  int n_seg;       // ceil(L / SEG_LEN)
-  long long rec0;  // first record of the item (within its wave)
-  long long stage; // byte offset of its staging (within its wave)
-};
-struct SegArgs {
-  const DeviceView* devs;
-  const WorkItem* items;
-  const SegItem* segs;     // the wave's items
-  const int* rec_item;     // per record of the wave: index into segs
-  long long n_rec;
-  int n_segitems;
-  double* rec;             // SEG_FIELDS x 32 doubles per record
-  unsigned char* stage;    // per item: L x (3 real axis | 2 contour) x 32 doubles
-  double* partial;
-  double* Tpart;
-  double* ring_cap;
-  int cap_ring;
-};
-size_t seg_stage_bytes(int L, int kind);
-// the five launches of one wave
-int launch_seg(const SegArgs& a, cudaStream_t s);
-
 struct ReduceDev {
   int n_rings, n_real, n_chains;
   int it0, it1;           // item range of the device
@@ -265,8 +234,7 @@ struct ReduceDev {
   double* T;
   double* I;
 };
-// second stage: one CTA column per device, ceil(max_rings / 256) CTAs (at most 1024) along its rings
-int launch_reduce(const ReduceDev* devs, int n_devs, int max_rings, cudaStream_t s);
+int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s);
 
 // Zero-bias conductance of one device (Eq. zeroBiasG): G = g_s (e^2/h) sum_k w_k T_k (-df/dE)(E_k - mu).
 struct CondDev {

@@ -978,9 +978,7 @@ int launch_plan(Ctx* c, Plan& P) {
     cudaEventRecord(e1, s);
     c->prof_events.emplace_back(e0, e1);
   }
-  int max_rings = 1;
-  for (const Dev* d : P.devs) max_rings = std::max(max_rings, d->n_rings);
-  if (launch_reduce((const ReduceDev*)B.reduce.p, (int)P.devs.size(), max_rings, s))
+  if (launch_reduce((const ReduceDev*)B.reduce.p, (int)P.devs.size(), s))
     return set_err(c, NEGF_ECUDA, "reduce launch failed");
   ++c->launches;
   return NEGF_OK;

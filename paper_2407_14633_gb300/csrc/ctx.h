@@ -13,6 +13,7 @@
 
 #include "../../include/negf.h"
 #include "common.cuh"
+#include "sweep_seg.cuh"
 
 namespace negf {
 

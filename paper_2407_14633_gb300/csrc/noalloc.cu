@@ -212,6 +212,6 @@ extern "C" int negf_chain1_compute_noalloc(void* stream, int n_rings, const doub
   a.status = reinterpret_cast<int*>(base + lo.counter) + 3;
   a.lane_stats = nullptr;
   if (launch_sweep_b1_f64(a, blocks, threads, s)) return NEGF_ECUDA;
-  if (launch_reduce(reinterpret_cast<const ReduceDev*>(base + lo.rdesc), 1, n_rings, s)) return NEGF_ECUDA;
+  if (launch_reduce(reinterpret_cast<const ReduceDev*>(base + lo.rdesc), 1, s)) return NEGF_ECUDA;
   return NEGF_OK;
 }

@@ -53,9 +53,9 @@ __global__ void __launch_bounds__(256) reduce_kernel(const ReduceDev* devs) {
   if (threadIdx.x == 0 && R.I) *R.I = 2.0 * kE2H * sh[0];
 }
 
-int launch_reduce(const ReduceDev* devs, int n_devs, int max_rings, cudaStream_t s) {
-  const int cols = std::max(1, std::min((max_rings + 255) / 256, 1024));
-  reduce_kernel<<<dim3(n_devs, cols), 256, 0, s>>>(devs);
+// 128 CTAs per device along its rings (a CTA past a short device's rings exits at once)
+int launch_reduce(const ReduceDev* devs, int n_devs, cudaStream_t s) {
+  reduce_kernel<<<dim3(n_devs, 128), 256, 0, s>>>(devs);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

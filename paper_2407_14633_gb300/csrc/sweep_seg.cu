@@ -21,7 +21,7 @@
 // recursion with the per-ring quadrature reduction of the thread-per-lane sweep.  The scans
 // are two-level: maps composed per chunk of segments, chained, then walked per chunk.  Segments
 // are fixed per device (SEG_LEN layers), so every result is the same in any batch.
-#include "common.cuh"
+#include "sweep_seg.cuh"
 #include "lead.cuh"
 
 namespace negf {
