@@ -1,4 +1,4 @@
-"""CPU check of the algebra behind the sweep split along the channel (row f5).
+"""CPU check of the algebra behind the sweep of 1 x 1 chains split along the channel.
 
 A plain numpy model of its five steps (per-segment Moebius maps of the forward recursion,
 their two-level scan, the re-run with per-segment affine maps of the backward update and the
