@@ -33,8 +33,8 @@ WORKLOAD = "cnt17_realspace_N512_E2048+128_sc"
 
 
 # DRAM traffic per launch of the block sweep, from one ncu capture of the N = 64 case with the
-# same energy grid (--profile-small), scaled by 512 / 64 layers (profiles/
-# sweep_blk_cnt17_N64_E2176_ncu.md).  It is reported only while the kernel sources hash to the
+# same energy grid (--profile-small), scaled by 512 / 64 layers: the staging traffic grows with
+# the layer count at a fixed grid.  It is reported only while the kernel sources hash to the
 # ones the capture was taken on.
 TRAFFIC_CAPTURE = {"sources_sha256": "d8432598cf4c31a2f738ff0ebf8fcc6dc99633fd9b74a70aa7cf34f3990fd7ab",
                    "bytes_per_launch": (1.120756e9 + 1.256483e9) * 512 / 64}
@@ -166,11 +166,26 @@ def build_workload(ctx, negf, synth, V_GS):
     return dev, w
 
 
-def cpu_sample(n_real=256, n_cont=16, chunk=16):
-    """The oracle as it stands on a bounded sample of the workload: the first n_real
-    real-axis energies and n_cont contour nodes of the full N = 512 device.  Runs in a
-    single-threaded subprocess; returns (seconds, ring-energy updates)."""
-    code = r"""
+def host_cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith(("model name", "cpu model")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+_ORACLE_WORKER = r"""
 import os, sys, time, json
 sys.path.insert(0, %r)
 from paper_2407_14633_gb300 import synth
@@ -178,42 +193,113 @@ from oracle import model, green, quadrature as q
 w = synth.realspace_17()
 ch = model.realspace_chain(17, w["t"], w["N"], w["U_S"], w["U_D"])
 g = q.bias_grid(w["mu_S"], w["mu_D"], w["kT"], w["n_real"], w["n_cont"], w["E_B"], w["eta"])
-t = time.perf_counter()
-for k0 in range(0, %d, %d):
-    green.rgf_lanes(ch, w["U"], g["E"][k0:k0 + %d] + 1j * g["eta"])
-for k0 in range(0, %d, %d):
-    green.rgf_lanes(ch, w["U"], g["z"][k0:k0 + %d], spectral=False)
-print(json.dumps(dict(seconds=time.perf_counter() - t, updates=w["N"] * (%d + %d))))
-""" % (ROOT, n_real, chunk, chunk, n_cont, chunk, chunk, n_real, n_cont)
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    if out.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + out.stderr[-2000:])
-    r = json.loads(out.stdout.strip().splitlines()[-1])
-    return r["seconds"], r["updates"]
+print("ready", flush=True)
+for line in sys.stdin:
+    job = json.loads(line)
+    k_lo, k_hi, c_lo, c_hi, chunk = job["k_lo"], job["k_hi"], job["c_lo"], job["c_hi"], job["chunk"]
+    while time.time() < job["t_start"]:
+        time.sleep(0.0005)
+    t0 = time.time()
+    for k0 in range(k_lo, k_hi, chunk):
+        green.rgf_lanes(ch, w["U"], g["E"][k0:min(k0 + chunk, k_hi)] + 1j * g["eta"])
+    for k0 in range(c_lo, c_hi, chunk):
+        green.rgf_lanes(ch, w["U"], g["z"][k0:min(k0 + chunk, c_hi)], spectral=False)
+    print(json.dumps(dict(start=t0, end=time.time(), updates=w["N"] * ((k_hi - k_lo) + (c_hi - c_lo)))),
+          flush=True)
+"""
+
+
+class OraclePool:
+    """`cores` single-threaded processes (one BLAS thread each, so each runs the oracle's own
+    arithmetic), each holding the N = 512 workload's chain and grid.  sample() splits a bounded
+    set of energies into contiguous slices; the processes start their slices together (a
+    shared wall-clock start) and the rate is every update over the span from that start to
+    the last process's end."""
+
+    def __init__(self, cores):
+        self.cores = max(1, cores)
+        env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        self.procs = [subprocess.Popen([sys.executable, "-c", _ORACLE_WORKER % ROOT], stdin=subprocess.PIPE,
+                                       stdout=subprocess.PIPE, text=True, env=env)
+                      for _ in range(self.cores)]
+        for p in self.procs:
+            if p.stdout.readline().strip() != "ready":
+                self.close()
+                raise RuntimeError("oracle worker failed to start")
+
+    def sample(self, n_real, n_cont, chunk=16):
+        """Returns (seconds, ring-energy updates) of the first n_real real-axis energies and
+        n_cont contour nodes."""
+        c = self.cores
+        t_start = time.time() + 0.2
+        for i, p in enumerate(self.procs):
+            job = dict(k_lo=n_real * i // c, k_hi=n_real * (i + 1) // c, c_lo=n_cont * i // c,
+                       c_hi=n_cont * (i + 1) // c, chunk=chunk, t_start=t_start)
+            p.stdin.write(json.dumps(job) + "\n")
+            p.stdin.flush()
+        res = [json.loads(p.stdout.readline()) for p in self.procs]
+        if min(r["start"] for r in res) < t_start - 1e-3:
+            raise RuntimeError("oracle workers did not start together")
+        return max(r["end"] for r in res) - t_start, sum(r["updates"] for r in res)
+
+    def close(self):
+        for p in self.procs:
+            try:
+                p.stdin.close()
+                p.wait(timeout=30)
+            except (OSError, subprocess.SubprocessError):
+                p.kill()
+
+
+def cpu_baseline_record(n_real=256, n_cont=16):
+    """cpu_baseline: the oracle on every host core, with the one-core figure beside it (the
+    same sample, one process)."""
+    cores = os.cpu_count() or 1
+    out = {}
+    for k in (cores, 1):
+        pool = OraclePool(k)
+        try:
+            pool.sample(k, 0)   # warm-up: one energy per process
+            out[k] = pool.sample(n_real, n_cont)
+        finally:
+            pool.close()
+    secs, upd = out[cores]
+    secs1, upd1 = out[1]
+    return {"value": upd / secs, "unit": "ring-energy updates/s", "cores": cores, "kind": "oracle",
+            "sample": "%d real-axis + %d contour energies of the N=512 workload, split over %d single-threaded "
+                      "processes" % (n_real, n_cont, cores),
+            "host_cpu": host_cpu_model(), "one_core": {"value": upd1 / secs1, "cores": 1}}
 
 
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    per_step = (32, 4)
-    for _ in range(args.warmup):
-        cpu_sample(*per_step)
-    secs, upd = 0.0, 0
-    for _ in range(args.steps):
-        s, u = cpu_sample(*per_step)
-        secs += s
-        upd += u
+    # each step: 32 real-axis + 4 contour energies per host core, at full N = 512
+    cores = os.cpu_count() or 1
+    per_step = (32 * cores, 4 * cores)
+    pool = OraclePool(cores)
+    try:
+        for _ in range(args.warmup):
+            pool.sample(*per_step)
+        secs, upd = 0.0, 0
+        for _ in range(args.steps):
+            s, u = pool.sample(*per_step)
+            secs += s
+            upd += u
+    finally:
+        pool.close()
     value = upd / secs
+    sample = "%d real-axis + %d contour energies of the N=512 workload per step, split over %d single-threaded " \
+             "processes" % (per_step[0], per_step[1], cores)
     line = {
         "impl": "reference", "metric": "RGF ring-energy updates/s", "value": value,
         "unit": "ring-energy updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample_per_step": "32 real-axis + 4 contour energies at full N=512"},
-        "cpu_baseline": {"value": value, "unit": "ring-energy updates/s", "cores": 1, "kind": "oracle",
-                         "sample": "32 real-axis + 4 contour energies of the N=512 workload per step"},
+        "config": {"workload": WORKLOAD, "sample_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": "ring-energy updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample, "host_cpu": host_cpu_model()},
         "e2e": {"value": value, "unit": "ring-energy updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -246,7 +332,8 @@ def run_ours(args):
 
     # ---- timed: K self-consistent iterations (graph replays); L2 flushed between steps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    M = min(256, args.warmup + args.steps + 2)
+    e2e_reps = max(2, min(args.steps, 5))
+    M = min(256, args.warmup + args.steps + e2e_reps + 4)
     ctx.sc_begin(dev, w["V_DS"], V_GS, w["U"], kappa, M=M, tol=1e-300)
     ctx.sc_step(dev, args.warmup, wait=True)
     barrier()
@@ -266,6 +353,28 @@ def run_ours(args):
     launches = ctx.launch_count() - l0
     clocks = clk.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+
+    # ---- end to end through the public API with host buffers: each step uploads the Broyden
+    #      state from pinned host memory (negf_sc_set_state), runs one self-consistent
+    #      iteration (the timed step's work) and reads the new state back (negf_sc_get_state)
+    st = ctx.sc_get_state(dev)
+    pinned = {k: torch.empty(st[k].size, dtype=torch.float64, pin_memory=True).numpy()
+              for k in ("n_in", "n_in_old", "f_old", "V", "W")}
+    for k in pinned:
+        pinned[k][:] = st[k].reshape(-1)
+    host_state = dict(pinned, m=st["m"])
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_reps):
+        flush.fill_(1.0)
+        ctx.sc_set_state(dev, host_state)
+        ctx.sc_step(dev, 1, wait=True)
+        st = ctx.sc_get_state(dev)
+        for k in pinned:
+            pinned[k][:] = st[k].reshape(-1)
+        host_state["m"] = st["m"]
+    t_e2e = (time.perf_counter() - t0) / e2e_reps
+    state_bytes = 8 * sum(v.size for v in pinned.values()) + 4
     ctx.sc_end(dev)
     t_max = max_over_ranks(ms, world)
     value = job_value(units_per_step, world, t_max)
@@ -295,9 +404,8 @@ def run_ours(args):
     traffic = (TRAFFIC_CAPTURE["bytes_per_launch"]
                if kernel_sources_sha256() == TRAFFIC_CAPTURE["sources_sha256"] else None)
 
-    # ---- end to end through the public API with host buffers
+    # ---- one NEGF evaluation through the public API with host buffers (no Poisson, no Broyden)
     U_host = np.ascontiguousarray(w["U"])
-    e2e_reps = max(2, min(args.steps, 5))
     ctx.set_potential(dev, U_host)
     ctx.compute([dev])
     torch.cuda.synchronize()
@@ -305,9 +413,7 @@ def run_ours(args):
     for _ in range(e2e_reps):
         ctx.set_potential(dev, U_host)
         r = ctx.compute([dev])[0]
-    t_e2e = (time.perf_counter() - t0) / e2e_reps
-    h2d = U_host.nbytes
-    d2h = 8 * (3 * N + n_real + 1)
+    t_eval = (time.perf_counter() - t0) / e2e_reps
 
     # ---- full bias-point solve to tolerance (the second metric)
     sc = None
@@ -329,14 +435,22 @@ def run_ours(args):
                    "energies_contour": n_cont, "step": "one self-consistent iteration (captured graph)",
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas per rank (weak)",
                    "launch_shape": ctx.blk_shape(17, 17)},
-        "e2e": {"value": units_per_step / t_e2e, "unit": "ring-energy updates/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "call": "negf_set_potential + negf_compute, host buffers"},
+        "e2e": {"value": units_per_step / t_e2e, "unit": "ring-energy updates/s",
+                "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+                "call": "negf_sc_set_state + negf_sc_step + negf_sc_get_state, pinned host buffers "
+                        "(the timed step's work plus the copies of its Broyden state)"},
+        "evaluation_e2e": {"value": units_per_step / t_eval, "unit": "ring-energy updates/s",
+                           "h2d_bytes_per_step": U_host.nbytes, "d2h_bytes_per_step": 8 * (3 * N + n_real + 1),
+                           "call": "negf_set_potential + negf_compute, host buffers: one NEGF evaluation "
+                                   "(no Poisson or Broyden)"},
         "gpu_launches": int(launches),
         "roofline": {"kernel": "sweep_blk_kernel", "bound": "alu", "achieved": achieved,
                      "peak": peak_derived, "unit": "TFLOP/s", "frac": achieved / peak_derived,
                      "peak_kind": "FP64 derived: 2 FMA/clk/SM x SMs x max SM clock",
                      "peak_probe": peak_probe, "frac_of_probe": achieved / peak_probe,
-                     "traffic": traffic, "kernel_ms": sweep_ms, "flops_per_launch": flops,
+                     "traffic": traffic,
+                     "traffic_note": "dram bytes of the N = 64 capture with the same grid, scaled by 512 / 64 layers",
+                     "kernel_ms": sweep_ms, "flops_per_launch": flops,
                      "lanes_per_launch": {"real_symmetric": lanes[0] // max(sweeps, 1),
                                           "real_general": lanes[1] // max(sweeps, 1),
                                           "contour_symmetric": lanes[2] // max(sweeps, 1),
@@ -354,9 +468,7 @@ def run_ours(args):
         pick = list(runs) if args.extras == "all" else args.extras.split(",")
         line["extras"] = {k: runs[k]() for k in pick}
     if rank == 0 and world == 1 and not args.no_cpu:
-        secs, upd = cpu_sample()
-        line["cpu_baseline"] = {"value": upd / secs, "unit": "ring-energy updates/s", "cores": 1,
-                                "kind": "oracle", "sample": "256 real-axis + 16 contour energies of the N=512 workload"}
+        line["cpu_baseline"] = cpu_baseline_record()
     ctx.close()
     if rank == 0:
         print(json.dumps(line))

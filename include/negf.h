@@ -467,11 +467,14 @@ int negf_request_times(negf_ctx* ctx, uint64_t ticket, double* t_submit, double*
  * where they run (code building a CUDA graph, allocator-free embedding hosts, tools that
  * only hand over pre-registered buffers).  The caller owns every input and output; the
  * library's scratch (work items, per-item ring sums, forward-sweep staging) lives in one
- * fixed 32 MiB device array that every GPU loading the library reserves until exit.  The
- * first call on a device looks up that array's address with the device current; make it
- * before any stream capture.  All calls share the array and it keeps the last call's
- * contents (what must start at zero is cleared on every call): calls that overlap on the
- * GPU race on it.  No cudaMalloc, cudaFree or other allocating routine is called.
+ * fixed 32 MiB device array that every GPU loading the library reserves until exit.  Each
+ * call made outside stream capture looks up that array's address with the device current;
+ * a call on a stream under capture reuses the address of the device's last uncaptured call
+ * (NEGF_EINVAL if there was none).  So make one call on each device before capturing, and
+ * again after a cudaDeviceReset, which may move the array.  All calls share the array and
+ * it keeps the last call's contents (what must start at zero is cleared on every call):
+ * calls that overlap on the GPU race on it.  No cudaMalloc, cudaFree or other allocating
+ * routine is called.
  *
  * stream: cudaStream_t to run on.  Device inputs: Hdiag (n_rings complex, H_{l,l} without
  * potential), U (n_rings), hsq (n_rings - 1, |H_{l,l+1}|^2), grid E, w, fS, fD (n_real) and
@@ -513,6 +516,17 @@ int negf_blk_width(negf_ctx* ctx, int fp32, int b, int m, int* warps, int* ctas_
 /* The CTA width (warps) the autotuner last chose for the thread-per-lane sweep of blocks of
  * width `block` (1 or 2) in FP64 (fp32 = 0) or FP32 (fp32 = 1); NEGF_EINVAL if none was tuned. */
 int negf_chain_width(negf_ctx* ctx, int fp32, int block, int* warps);
+
+/* Wave planner of the sweep split along the channel (host only; needs no device or context).
+ * Split items are taken in order; consecutive items share a wave while their staging fits
+ * `cap` bytes (an item alone may exceed it and then forms a wave of its own).  Item i has
+ * stage[i] bytes of staging and n_seg[i] >= 1 segment records.  wave_of[i] receives the wave
+ * of item i, *max_stage the largest staging of a wave and *max_records the most records a
+ * wave holds: negf_compute sizes its record buffer by that figure for the partition it
+ * finally uses (under an HBM budget, a partition at the budget's cap).  NEGF_EINVAL for a
+ * negative size or cap, or a missing array. */
+int negf_plan_seg_waves(int n, const long long* stage, const int* n_seg, long long cap, int* wave_of,
+                        long long* max_stage, long long* max_records);
 
 /* Measured FP64 FMA throughput of this GPU (TFLOP/s): a register-resident FMA loop over
  * every SM, best of three, for the FP64 roofline of the sweep kernels. */

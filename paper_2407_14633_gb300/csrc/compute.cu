@@ -36,6 +36,38 @@ int chain_bucket(int n) {
 
 }  // namespace
 
+// Waves of the sweep split along the channel: consecutive items whose staging fits cap (an
+// item alone may exceed it and then forms a wave of its own).  Sets each item's first record
+// and staging offset within its wave, fills `waves`, and returns the largest staging of a
+// wave; *max_recs receives the most records any wave holds (the record buffer's size).
+long long seg_partition(std::vector<SegItem>& seg, const std::vector<long long>& stage, long long cap,
+                        std::vector<Plan::SegWave>& waves, long long* max_recs) {
+  waves.clear();
+  long long st = 0, rec = 0, r0 = 0, worst = 0, most = 0;
+  int i0 = 0;
+  for (int j = 0; j < (int)seg.size(); ++j) {
+    if (j > i0 && st + stage[j] > cap) {
+      waves.push_back({i0, j - i0, r0, rec});
+      most = std::max(most, rec);
+      r0 += rec;
+      i0 = j;
+      st = 0;
+      rec = 0;
+    }
+    seg[j].rec0 = rec;
+    seg[j].stage = st;
+    st += stage[j];
+    rec += seg[j].n_seg;
+    worst = std::max(worst, st);
+  }
+  if (!seg.empty()) {
+    waves.push_back({i0, (int)seg.size() - i0, r0, rec});
+    most = std::max(most, rec);
+  }
+  if (max_recs) *max_recs = most;
+  return worst;
+}
+
 
 DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
   DeviceView v;
@@ -582,43 +614,22 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       }
     }
 
-  // split items in waves: consecutive items whose staging fits cap (an item alone may not);
-  // returns the largest staging of a wave and sets the records of the largest wave
+  // split items in waves (seg_partition); the record buffer holds the largest wave's records
+  std::vector<long long> seg_stage(P.seg.size());
+  for (size_t j = 0; j < P.seg.size(); ++j) {
+    const WorkItem& W = items[P.seg[j].item];
+    seg_stage[j] = (long long)seg_stage_bytes(P.views[W.dev].L, W.kind);
+  }
   long long seg_recs = 0;
   auto seg_waves = [&](long long cap) -> long long {
-    P.seg_waves.clear();
-    seg_recs = 0;
-    long long st = 0, rec = 0, r0 = 0, worst = 0;
-    int i0 = 0;
-    for (int j = 0; j < (int)P.seg.size(); ++j) {
-      SegItem& S = P.seg[j];
-      const WorkItem& W = items[S.item];
-      const long long b = (long long)seg_stage_bytes(P.views[W.dev].L, W.kind);
-      if (j > i0 && st + b > cap) {
-        P.seg_waves.push_back({i0, j - i0, r0, rec});
-        seg_recs = std::max(seg_recs, rec);
-        r0 += rec;
-        i0 = j;
-        st = 0;
-        rec = 0;
-      }
-      S.rec0 = rec;
-      S.stage = st;
-      st += b;
-      rec += S.n_seg;
-      worst = std::max(worst, st);
-    }
-    if (!P.seg.empty()) {
-      P.seg_waves.push_back({i0, (int)P.seg.size() - i0, r0, rec});
-      seg_recs = std::max(seg_recs, rec);
-    }
-    return worst;
+    return seg_partition(P.seg, seg_stage, cap, P.seg_waves, &seg_recs);
   };
   constexpr long long SEG_WAVE_BYTES = 4LL << 30;
   stage_bytes = std::max(stage_bytes, seg_waves(SEG_WAVE_BYTES));
   long long seg_rec_total = 0;
   for (const SegItem& S : P.seg) seg_rec_total += S.n_seg;
-  const size_t segrec_bytes = (size_t)std::max<long long>(seg_recs * SEG_FIELDS * 32 * 8, 16);
+  auto segrec_size = [](long long recs) { return (size_t)std::max<long long>(recs * SEG_FIELDS * 32 * 8, 16); };
+  size_t segrec_bytes = segrec_size(seg_recs);
   const size_t segitem_bytes = std::max<size_t>(sizeof(SegItem) * P.seg.size(), 16);
   const size_t recitem_bytes = (size_t)std::max<long long>(seg_rec_total * 4, 16);
 
@@ -646,7 +657,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
                       extra(B.tpart, sizeof(double) * std::max<long long>(tpos, 1)) + extra(B.reduce, sizeof(ReduceDev) * nd) +
                       extra(B.counter, sizeof(int) * 16) + extra(B.status, sizeof(int)) + extra(B.hu, hu_bytes) +
                       extra(B.prep, prep_bytes) + extra(B.segitems, segitem_bytes) + extra(B.recitem, recitem_bytes) +
-                      extra(B.segrec, segrec_bytes);
+                      extra(B.segrec, segrec_size(seg_rec_total));
     if (P.prec != NEGF_PREC_FP64)
       other += extra(B.resid, sizeof(double) * tpos) + extra(B.growth, sizeof(double) * tpos) + extra(B.order2, sizeof(int) * n_items);
     for (int di = 0; di < nd; ++di) {
@@ -672,6 +683,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
         const long long sw = seg_waves(cap);
         if (sw > cap) return set_err(c, NEGF_ENOMEM, "budget too small for the staging of one split chain");
         stage_bytes = std::max(stage_bytes, sw);
+        segrec_bytes = segrec_size(seg_recs);   // the records of the final partition's largest wave
       }
     }
   }
@@ -1335,6 +1347,27 @@ int negf_kernel_time(negf_ctx* c, double* sweep_ms, uint64_t* sweeps) {
   *sweeps = c->prof_count;
   c->prof_ms = 0.0;
   c->prof_count = 0;
+  return NEGF_OK;
+}
+
+int negf_plan_seg_waves(int n, const long long* stage, const int* n_seg, long long cap, int* wave_of,
+                        long long* max_stage, long long* max_records) {
+  if (n < 0 || (n > 0 && (!stage || !n_seg || !wave_of)) || cap < 0) return NEGF_EINVAL;
+  std::vector<SegItem> seg((size_t)n);
+  std::vector<long long> st((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    if (stage[i] < 0 || n_seg[i] < 1) return NEGF_EINVAL;
+    seg[i].item = i;
+    seg[i].n_seg = n_seg[i];
+    st[i] = stage[i];
+  }
+  std::vector<Plan::SegWave> waves;
+  long long recs = 0;
+  const long long worst = seg_partition(seg, st, cap, waves, &recs);
+  for (int w = 0; w < (int)waves.size(); ++w)
+    for (int j = 0; j < waves[w].ni; ++j) wave_of[waves[w].i0 + j] = w;
+  if (max_stage) *max_stage = worst;
+  if (max_records) *max_records = recs;
   return NEGF_OK;
 }
 

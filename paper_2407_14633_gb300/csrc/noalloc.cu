@@ -9,8 +9,11 @@
 // memory they own; this entry point allocates nothing and calls no allocating routine.
 //
 // The array (NOALLOC_SCRATCH_BYTES) is reserved on every GPU that loads the library,
-// until process exit.  Its device address is looked up once per device, on the first call
-// with that device current; make that first call before any stream capture.  All calls
+// until process exit.  Its device address is looked up with the device current on every
+// call made outside stream capture (a lookup is cheap and picks up a new address after a
+// device reset reloaded the module); a call made while its stream is being captured uses the
+// address of the device's last uncaptured call.  So make a first call on each device, and
+// again after any cudaDeviceReset, before capturing one.  All calls
 // share the array and it keeps the previous call's contents, so the set-up kernel clears
 // what must start at zero (the work counter and the T(E) partials), and calls that overlap
 // on the GPU (different streams, or different host threads on one device) race on it.
@@ -92,12 +95,20 @@ __global__ void noalloc_setup_kernel(unsigned char* base, NoallocLayout lo, Devi
   }
 }
 
-// Device address of the scratch for the current device (looked up on first use).
-int scratch_address(unsigned char** out) {
+// Device address of the scratch for the current device: looked up again unless `s` is being
+// captured (then the address of the last uncaptured call on this device; none is an error).
+int scratch_address(cudaStream_t s, unsigned char** out) {
   int d = 0;
   if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return NEGF_ECUDA;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return NEGF_ECUDA;
+  }
   std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_ptr[d]) {
+  if (cs != cudaStreamCaptureStatusNone) {
+    if (!g_noalloc_ptr[d]) return NEGF_EINVAL;   // no uncaptured call on this device yet
+  } else {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
@@ -125,10 +136,10 @@ extern "C" int negf_chain1_compute_noalloc(void* stream, int n_rings, const doub
   if (n_real < 0 || n_cont < 0 || n_real + n_cont == 0) return NEGF_EINVAL;
   if (n_real > 0 && (!E || !w || !fS || !fD || !(eta > 0.0))) return NEGF_EINVAL;
   if (n_cont > 0 && (!z || !c)) return NEGF_EINVAL;
-  unsigned char* base = nullptr;
-  int rc = scratch_address(&base);
-  if (rc) return rc;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char* base = nullptr;
+  int rc = scratch_address(s, &base);
+  if (rc) return rc;
   const int items_real = (n_real + LANES - 1) / LANES, items_cont = (n_cont + LANES - 1) / LANES;
   const int n_items = items_real + items_cont;
   // as many resident warps as items, occupancy and the fixed scratch allow

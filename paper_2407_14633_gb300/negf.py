@@ -132,6 +132,8 @@ _PROTOS = {
     "negf_sweep_lanes": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint64)]),
     "negf_blk_width": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int, _ip, _ip]),
     "negf_chain_width": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _ip]),
+    "negf_plan_seg_waves": (C.c_int, [C.c_int, C.POINTER(C.c_longlong), _ip, C.c_longlong, _ip,
+                                      C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "negf_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)]),
     "negf_serve_step": (C.c_int, [C.c_void_p, _ip]),
     "negf_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(ScResult)]),
@@ -233,6 +235,21 @@ def make_grid_adaptive(mu_S, mu_D, kT, eta, E_B, n_cont, E_l1, E_l2, densities, 
     if rc:
         raise NegfError(rc, "make_grid_adaptive")
     return dict(E=E, w=w, fS=fS, fD=fD, z=z.view(np.complex128)[:n_cont], c=c.view(np.complex128)[:n_cont], eta=eta)
+
+
+def plan_seg_waves(stage_bytes, n_seg, cap):
+    """negf_plan_seg_waves (host only): wave of each split item, largest wave staging, most
+    records of a wave."""
+    lib = load()
+    st = np.ascontiguousarray(stage_bytes, dtype=np.int64)
+    ns = np.ascontiguousarray(n_seg, dtype=np.int32)
+    wave = np.zeros(max(st.size, 1), dtype=np.int32)
+    mst, mrec = C.c_longlong(), C.c_longlong()
+    rc = lib.negf_plan_seg_waves(st.size, st.ctypes.data_as(C.POINTER(C.c_longlong)), _pi(ns), int(cap), _pi(wave),
+                                 C.byref(mst), C.byref(mrec))
+    if rc:
+        raise NegfError(rc, lib.negf_strerror(rc).decode())
+    return wave[:st.size], mst.value, mrec.value
 
 
 def poisson_kappa(eps_r=3.9, d_nm=1.3, t_ox_nm=10.0, dx_nm=0.1065):

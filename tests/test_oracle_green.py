@@ -22,6 +22,8 @@ def chains_under_test():
         ("cells2x2", mdl.mode_chain_cells(17, 5, T_HOP, 8, 0.0, -0.2), U8),
         ("real5", mdl.realspace_chain(5, T_HOP, 6, 0.0, -0.1), U8[:6]),
         ("real17", mdl.realspace_chain(17, T_HOP, 4, 0.02, -0.1), U8[:4]),
+        ("real26", mdl.realspace_chain(26, T_HOP, 3, 0.0, -0.1), U8[:3]),
+        ("real34", mdl.realspace_chain(34, T_HOP, 3, 0.03, -0.05), U8[:3]),
     ]
 
 
