@@ -566,9 +566,12 @@ int negf_set_lead(negf_ctx* c, int dev, int chain, int side, const negf_lead* le
     return set_err(c, NEGF_EINVAL, "bad lead arguments");
   if (d->block <= 2 && lead->m != 1)
     return set_err(c, NEGF_EINVAL, "blocks of width 1 or 2 take single-site leads");
-  for (int s = 0; s < lead->m; ++s)
+  for (int s = 0; s < lead->m; ++s) {
     if (lead->sites[s] < 0 || lead->sites[s] >= d->block)
       return set_err(c, NEGF_EINVAL, "lead site outside the boundary layer");
+    for (int t = 0; t < s; ++t)
+      if (lead->sites[t] == lead->sites[s]) return set_err(c, NEGF_EINVAL, "lead site listed twice");
+  }
   HostLead& L = d->ch[chain].lead[side];
   L.gen = false;
   L.m = lead->m;

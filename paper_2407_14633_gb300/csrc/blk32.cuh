@@ -1,0 +1,18 @@
+// Host entry points of the register-tiled complex64 sweep of wide ring blocks
+// (sweep_block32.cu).
+#pragma once
+#include "common.cuh"
+
+namespace negf {
+
+// Tile class (CTA width in warps: 1, 2 or 4) that runs blocks of width b with leads of m
+// sites at a requested width: the smallest class holding b x b that is at least that wide;
+// 0 when no class holds b (b > 36) or m > b.
+int blk32_class(int b, int m, int warps);
+size_t blk32_smem_bytes(int nw);
+// staging bytes per layer of one lane (gL_l and R_l tiles)
+long long blk32_stage_layer_bytes(int nw);
+int blk32_occupancy(int nw);
+int launch_blk32(const SweepArgs& a, int grid, int nw, cudaStream_t s);
+
+}  // namespace negf

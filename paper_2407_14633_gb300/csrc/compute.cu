@@ -12,6 +12,7 @@
 #include <cstring>
 #include <numeric>
 
+#include "blk32.cuh"
 #include "ctx.h"
 
 namespace negf {
@@ -213,9 +214,36 @@ static int cap_rule(long long n, int sms, int occ) {
   return occ;
 }
 
+// Wide-block sweep kernels: complex64 blocks that a tile class holds run the register-tiled
+// kernel (sweep_block32.cu) at that class's width (at least the requested one); the rest run
+// the shared-memory kernel of sweep_block.cu.
+static int blk32_of(bool f32, int b, int m, int w) { return f32 ? blk32_class(b, m, w) : 0; }
+static int blk_eff_width(bool f32, int b, int m, int w) {
+  const int k = blk32_of(f32, b, m, w);
+  return k ? k : w;
+}
+static size_t blk_smem(bool f32, int b, int m, int w) {
+  const int k = blk32_of(f32, b, m, w);
+  return k ? blk32_smem_bytes(k) : sweep_blk_smem_bytes_t(b, m, f32 ? 8 : 16, w);
+}
+static int blk_occupancy(bool f32, int w, int b, int m) {
+  const int k = blk32_of(f32, b, m, w);
+  return k ? blk32_occupancy(k) : sweep_blk_occupancy_t(f32, w, b, m);
+}
+static int blk_launch(bool f32, const SweepArgs& a, int b, int m, int grid, int w, cudaStream_t s) {
+  const int k = blk32_of(f32, b, m, w);
+  return k ? launch_blk32(a, grid, k, s) : launch_sweep_blk_t(f32, a, b, m, grid, w, s);
+}
+// staging bytes per layer of one wide-block lane: FP64 gL_l and R_l (the FP64 sweep and the
+// mixed path's recompute), or the tiles of the complex64 kernel at width w
+static long long blk_layer_bytes(bool f32, int b, int m, int w) {
+  const int k = blk32_of(f32, b, m, w);
+  return k ? blk32_stage_layer_bytes(k) : (long long)(b * b + b * m) * 16;
+}
+
 static int blk_occ(Ctx* c, bool f32, int w, int b, int m) {
-  if (sweep_blk_smem_bytes_t(b, m, f32 ? 8 : 16, w) > 227 * 1024) return 0;
-  int occ = sweep_blk_occupancy_t(f32, w, b, m);
+  if (blk_smem(f32, b, m, w) > 227 * 1024) return 0;
+  int occ = blk_occupancy(f32, w, b, m);
   if (c->opts.blk_ctas_per_sm > 0) occ = std::min(occ, c->opts.blk_ctas_per_sm);
   return occ;
 }
@@ -249,6 +277,7 @@ static int tune_width(Ctx* c, Plan& P, int g) {
   };
   std::vector<Cand> cand;
   for (int w : {1, 2, 4}) {
+    if (blk_eff_width(f32, P.gb[g], P.gm[g], w) != w) continue;   // the same kernel as a wider width
     const int occ = blk_occ(c, f32, w, P.gb[g], P.gm[g]);
     if (occ < 1) continue;
     for (int cap : {occ, cap_rule(n, c->sms, occ)}) {
@@ -271,7 +300,7 @@ static int tune_width(Ctx* c, Plan& P, int g) {
     if (!has) continue;
     const SweepArgs a = group_args(P, g, order, 1, nullptr, nullptr);
     if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess ||
-        launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], 1, w, s)) {
+        blk_launch(f32, a, P.gb[g], P.gm[g], 1, w, s)) {
       rc = set_err(c, NEGF_ECUDA, "tuning launch failed");
       break;
     }
@@ -282,7 +311,7 @@ static int tune_width(Ctx* c, Plan& P, int g) {
   for (size_t i = 0; i < cand.size() && !rc; ++i) {
     const SweepArgs a = group_args(P, g, order, n, nullptr, nullptr);
     if (cudaMemsetAsync(a.counter, 0, sizeof(int), s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
-        launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], cand[i].grid, cand[i].w, s) ||
+        blk_launch(f32, a, P.gb[g], P.gm[g], cand[i].grid, cand[i].w, s) ||
         cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
       rc = set_err(c, NEGF_ECUDA, "tuning launch failed");
       break;
@@ -566,7 +595,17 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     const int L = Lmax[g % 5];
     if (cls == 0) P.stride[g] = (long long)L * 5 * 32 * 8;
     else if (cls == 1) P.stride[g] = (long long)L * 12 * 32 * 8;
-    else P.stride[g] = (long long)L * (P.gb[g] * P.gb[g] + P.gb[g] * P.gm[g]) * 16;
+    else {
+      // one stride serves the FP64 group g % 5 and its FP32 group g % 5 + 5 (whose items the
+      // mixed path recomputes in FP64): the larger of their per-layer needs, at every width
+      // the FP32 group may run (all trial widths when it is tuned)
+      const int g5 = g % 5, gf = g5 + 5;
+      long long per = blk_layer_bytes(false, P.gb[g5], P.gm[g5], 1);
+      if (P.ncls[gf])
+        for (int w : {1, 2, 4})
+          if (tune_g[gf] || w == P.gw[gf]) per = std::max(per, blk_layer_bytes(true, P.gb[gf], P.gm[gf], w));
+      P.stride[g] = (long long)L * per;
+    }
     P.grid[g] = 0;
     if (!P.ncls[g]) continue;
     const bool f32 = group_f32(g);
@@ -581,7 +620,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
           stage_bytes = std::max(stage_bytes, P.stride[g] * warps);
         }
     } else {
-      const size_t sm = sweep_blk_smem_bytes_t(P.gb[g], P.gm[g], f32 ? 8 : 16, P.gw[g]);
+      const size_t sm = blk_smem(f32, P.gb[g], P.gm[g], P.gw[g]);
       if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
       const int occ = blk_occ(c, f32, P.gw[g], P.gb[g], P.gm[g]);
       per_sm = P.gcap[g] > 0 ? std::min(occ, P.gcap[g]) : cap_rule(P.ncls[g], c->sms, occ);
@@ -867,7 +906,7 @@ static int launch_group(Ctx* c, const Plan& P, int g, const int* order, int n, i
     rc = f32 ? launch_sweep_b2_f32(a, grid, 32 * (warps > 0 ? warps : P.gw[g]), s)
              : launch_sweep_b2_f64(a, grid, 32 * (warps > 0 ? warps : P.gw[g]), s);
   else
-    rc = launch_sweep_blk_t(f32, a, P.gb[g], P.gm[g], grid, warps > 0 ? warps : P.gw[g], s);
+    rc = blk_launch(f32, a, P.gb[g], P.gm[g], grid, warps > 0 ? warps : P.gw[g], s);
   if (rc) return set_err(c, NEGF_ECUDA, "sweep launch failed");
   ++c->launches;
   return NEGF_OK;
