@@ -187,25 +187,69 @@ def host_cpu_model():
 
 _ORACLE_WORKER = r"""
 import os, sys, time, json
+import numpy as np
 sys.path.insert(0, %r)
 from paper_2407_14633_gb300 import synth
 from oracle import model, green, quadrature as q
-w = synth.realspace_17()
-ch = model.realspace_chain(17, w["t"], w["N"], w["U_S"], w["U_D"])
-g = q.bias_grid(w["mu_S"], w["mu_D"], w["kT"], w["n_real"], w["n_cont"], w["E_B"], w["eta"])
+
+def build(name):
+    # (chains of the oracle device, potential, grid) of a named workload
+    if name == "cfg2":
+        w = synth.realspace_17()
+        dev = model.cnt_build("real", 17, w["t"], w["N"], w["U_S"], w["U_D"])
+        g = q.bias_grid(w["mu_S"], w["mu_D"], w["kT"], w["n_real"], w["n_cont"], w["E_B"], w["eta"])
+        return dev, w["U"], g
+    if name == "cfg1":
+        w = synth.modespace_small(6)
+        dev = model.cnt_build("mode", w["n_tube"], w["t"], w["N"], w["U_S"], w["U_D"], modes=(6,))
+        g = q.bias_grid(w["mu_S"], w["mu_D"], w["kT"], w["n_real"], w["n_cont"], w["E_B"], w["eta"],
+                        rule="midpoint", E_min=-1.0, E_max=1.0)
+        return dev, w["U"], g
+    if name.startswith("cfg3_"):
+        w = synth.batched_uneven()
+        d = w["devices"][int(name[5:])]
+        dev = model.cnt_build("mode", w["n_tube"], w["t"], d["N"], 0.0, -d["V_DS"], modes=tuple(d["modes"]),
+                              cells=d["block"] == 2)
+        g = q.bias_grid(0.0, -d["V_DS"], w["kT"], d["n_real"], d["n_cont"], d["E_B"], w["eta"])
+        return dev, d["U"], g
+    if name == "cfg4":
+        w = synth.mixed_precision(n_tube=17, N=1024, n_energies=4096)
+        dev = model.cnt_build("real", 17, w["t"], w["N"], w["U_S"], w["U_D"])
+        E = w["E"]
+        E_B = float(np.min(w["U"]) - 3.0 * abs(w["t"]) - 1.0)
+        z, c = q.contour_semicircle(E_B, -1.0, 64)
+        g = dict(E=E, w=np.full(E.size, 2.0 / E.size), fS=q.fermi(E - w["mu_S"], w["kT"]),
+                 fD=q.fermi(E - w["mu_D"], w["kT"]), eta=w["eta"], z=z, c=c)
+        return dev, w["U"], g
+    if name == "cfg5":
+        w = synth.serving_sweep()
+        r = w["requests"][0]
+        dev = model.cnt_build("mode", w["n_tube"], w["t"], r["N"], 0.0, -r["V_DS"], modes=tuple(r["modes"]))
+        E_B = -r["V_DS"] - 3.0 * abs(w["t"]) - 1.0
+        g = q.bias_grid(0.0, -r["V_DS"], w["kT"], r["n_real"], r["n_cont"], E_B, w["eta"])
+        return dev, np.linspace(0.0, -r["V_DS"], r["N"]), g
+    raise ValueError(name)
+
+cases = {}
 print("ready", flush=True)
 for line in sys.stdin:
     job = json.loads(line)
+    if job["case"] not in cases:
+        cases[job["case"]] = build(job["case"])
+    dev, U, g = cases[job["case"]]
     k_lo, k_hi, c_lo, c_hi, chunk = job["k_lo"], job["k_hi"], job["c_lo"], job["c_hi"], job["chunk"]
+    k_hi, c_hi = min(k_hi, g["E"].size), min(c_hi, g["z"].size)
     while time.time() < job["t_start"]:
         time.sleep(0.0005)
     t0 = time.time()
-    for k0 in range(k_lo, k_hi, chunk):
-        green.rgf_lanes(ch, w["U"], g["E"][k0:min(k0 + chunk, k_hi)] + 1j * g["eta"])
-    for k0 in range(c_lo, c_hi, chunk):
-        green.rgf_lanes(ch, w["U"], g["z"][k0:min(k0 + chunk, c_hi)], spectral=False)
-    print(json.dumps(dict(start=t0, end=time.time(), updates=w["N"] * ((k_hi - k_lo) + (c_hi - c_lo)))),
-          flush=True)
+    for _ in range(job.get("reps", 1)):
+        for ch in dev.chains:
+            for k0 in range(k_lo, k_hi, chunk):
+                green.rgf_lanes(ch, U, g["E"][k0:min(k0 + chunk, k_hi)] + 1j * g["eta"])
+            for k0 in range(c_lo, c_hi, chunk):
+                green.rgf_lanes(ch, U, g["z"][k0:min(k0 + chunk, c_hi)], spectral=False)
+    units = job.get("reps", 1) * dev.n_rings * len(dev.chains) * (max(k_hi - k_lo, 0) + max(c_hi - c_lo, 0))
+    print(json.dumps(dict(start=t0, end=time.time(), updates=units)), flush=True)
 """
 
 
@@ -227,14 +271,16 @@ class OraclePool:
                 self.close()
                 raise RuntimeError("oracle worker failed to start")
 
-    def sample(self, n_real, n_cont, chunk=16):
-        """Returns (seconds, ring-energy updates) of the first n_real real-axis energies and
-        n_cont contour nodes."""
+    def sample(self, n_real, n_cont, chunk=16, case="cfg2", k0=0, c0=0, reps=1):
+        """Returns (seconds, ring-energy(-mode) updates) of n_real real-axis energies from index
+        k0 and n_cont contour nodes from c0 of a named workload (default: the bench workload),
+        each process repeating its slice reps times."""
         c = self.cores
         t_start = time.time() + 0.2
         for i, p in enumerate(self.procs):
-            job = dict(k_lo=n_real * i // c, k_hi=n_real * (i + 1) // c, c_lo=n_cont * i // c,
-                       c_hi=n_cont * (i + 1) // c, chunk=chunk, t_start=t_start)
+            job = dict(case=case, k_lo=k0 + n_real * i // c, k_hi=k0 + n_real * (i + 1) // c,
+                       c_lo=c0 + n_cont * i // c, c_hi=c0 + n_cont * (i + 1) // c, chunk=chunk, t_start=t_start,
+                       reps=reps)
             p.stdin.write(json.dumps(job) + "\n")
             p.stdin.flush()
         res = [json.loads(p.stdout.readline()) for p in self.procs]
@@ -269,6 +315,31 @@ def cpu_baseline_record(n_real=256, n_cont=16):
             "sample": "%d real-axis + %d contour energies of the N=512 workload, split over %d single-threaded "
                       "processes" % (n_real, n_cont, cores),
             "host_cpu": host_cpu_model(), "one_core": {"value": upd1 / secs1, "cores": 1}}
+
+
+def cpu_configs():
+    """The oracle on every host core, on bounded samples of each workload (ring-energy(-mode)
+    updates per second): the small mode-space case in full, one device of the uneven batch per
+    block form, and energy samples of the bench, mixed-precision and serving workloads.  A sample
+    of a few energies stands for the whole grid; the oracle's cost per update does not depend on
+    which energies it takes."""
+    cores = os.cpu_count() or 1
+    pool = OraclePool(cores)
+    out = {"cores": cores, "host_cpu": host_cpu_model()}
+    try:
+        plan = [("cfg1", "small mode space N=64, j=6: all 256 + 64 energies, 100 times", 256, 64, 0, 0, 100),
+                ("cfg2", "real space 17x17 N=512: 256 + 16 energies", 256, 16, 0, 0, 1),
+                ("cfg3_0", "uneven batch, device 0: 48 + 4 energies per core", 48 * cores, 4 * cores, 0, 0, 1),
+                ("cfg3_1", "uneven batch, device 1: 48 + 4 energies per core", 48 * cores, 4 * cores, 0, 0, 1),
+                ("cfg4", "(17,0) N=1024, band-edge grid: 8 energies per core", 8 * cores, 0, 1000, 0, 1),
+                ("cfg5", "serving request 0 (2 modes): 96 + 4 energies per core", 96 * cores, 4 * cores, 0, 0, 1)]
+        for case, what, nr, nc, k0, c0, reps in plan:
+            pool.sample(min(nr, cores), 0, case=case, k0=k0)   # warm-up, builds the case
+            secs, upd = pool.sample(nr, nc, case=case, k0=k0, c0=c0, reps=reps)
+            out[case] = {"updates_per_s": upd / secs, "sample": what, "seconds": secs}
+    finally:
+        pool.close()
+    return out
 
 
 def run_reference(args):
@@ -458,14 +529,39 @@ def run_ours(args):
         "clocks": clocks,
         "self_consistent_solve": sc,
     }
+    from paper_2407_14633_gb300 import workloads
+    if rank == 0 and world == 1 and not args.no_workloads:
+        # the mixed-precision and serving workloads at reduced size beside the headline
+        mp = workloads.mixed_precision(tubes=(17,), variants=((0.002, 0.0, 1e-4),))["(17,0)"]
+        d = mp["mixed_w0.002_g0_r0.0001"]
+        line["mixed"] = {"workload": "cnt17_realspace_N1024_E4096_bandedge", "c128_sweep_ms": mp["c128_sweep_ms"],
+                         "mixed_sweep_ms": d["sweep_ms"], "speedup_vs_c128": d["speedup_vs_c128"],
+                         "recomputed_fraction": d["recomputed_fraction"],
+                         "rel_err_vs_c128": {"n": d["rel_err_n"], "T": d["rel_err_T"], "I": d["rel_err_I"]},
+                         "c64_only": {"speedup_vs_c128": mp["c64"]["speedup_vs_c128"],
+                                      "rel_err_vs_c128": {"n": mp["c64"]["rel_err_n"], "T": mp["c64"]["rel_err_T"],
+                                                          "I": mp["c64"]["rel_err_I"]}},
+                         "options": "flag_threshold 1e-4, edge_window 2 meV, growth criterion off"}
+        sv = workloads.serving_sweep(n_requests=args.serving_requests)
+        line["serving"] = {"workload": "iv_sweep_first%d_of_256_requests" % args.serving_requests,
+                           "requests": sv["requests"], "converged": sv["converged_requests"], "tol": sv["tol"],
+                           "bias_points_per_s": {"sequential": sv["sequential_bias_points_per_s"],
+                                                 "served": sv["served_bias_points_per_s"],
+                                                 "saturated": sv["saturated_bias_points_per_s"]},
+                           "converged_bias_points_per_s": sv["converged_bias_points_per_s"],
+                           "served_p50_s": sv["served_p50_s"], "served_p99_s": sv["served_p99_s"],
+                           "sequential_queued_p50_s": sv["sequential_queued_p50_s"],
+                           "sequential_queued_p99_s": sv["sequential_queued_p99_s"],
+                           "arrival_rate_per_s": sv["arrival_rate_per_s"],
+                           "bitwise_same_as_sequential": sv["bitwise_same_as_sequential"]}
     if args.extras and rank == 0:
-        from paper_2407_14633_gb300 import workloads
         runs = {"modespace_small": workloads.modespace_small, "batched_uneven": workloads.batched_uneven,
                 "mixed_precision": workloads.mixed_precision, "serving": workloads.serving_sweep,
                 "gate_sweep": lambda: {"warm": workloads.gate_sweep(), "cold": workloads.gate_sweep(warm=False)},
                 "adaptive_grid": workloads.adaptive_grid, "multichannel": workloads.multichannel,
-                "general_leads": workloads.general_leads, "paper_scaling": workloads.paper_scaling}
-        pick = list(runs) if args.extras == "all" else args.extras.split(",")
+                "general_leads": workloads.general_leads, "paper_scaling": workloads.paper_scaling,
+                "cpu_configs": cpu_configs}
+        pick = [k for k in runs if k != "cpu_configs"] if args.extras == "all" else args.extras.split(",")
         line["extras"] = {k: runs[k]() for k in pick}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_record()
@@ -545,10 +641,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the reduced mixed-precision and serving workloads of the default line")
+    ap.add_argument("--serving-requests", type=int, default=48,
+                    help="requests of the seeded serving stream in the default line (its first ones)")
     ap.add_argument("--extras", nargs="?", const="all", default=None,
                     help="also run the small, batched-uneven, mixed-precision, serving and gate-sweep workloads "
                          "(or a comma list of modespace_small, batched_uneven, mixed_precision, serving, "
-                         "gate_sweep, adaptive_grid, multichannel, general_leads, paper_scaling)")
+                         "gate_sweep, adaptive_grid, multichannel, general_leads, paper_scaling, cpu_configs; "
+                         "cpu_configs times the oracle on every host core on samples of each workload)")
     ap.add_argument("--profile-small", action="store_true",
                     help="reduced case of the block sweep for ncu captures")
     ap.add_argument("--blk-warps", type=int, default=1,
