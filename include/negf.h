@@ -90,7 +90,12 @@ typedef struct negf_ctx negf_ctx;
  * recursions: 0 = for devices with at least 16384 layers and at most 128 such 32-energy items
  * of their own (long channels, few energies), 1 = for every 1 x 1 chain, -1 = never.  The choice
  * is made per device, so a device's results do not depend on its batch; they differ from the
- * unsplit sweep by rounding only. */
+ * unsplit sweep by rounding only.  mixed_two_pass: mixed precision, 1 = recompute flagged
+ * energies of ring blocks in a second FP64 pass after the complex64 sweep; 0 = re-sweep a
+ * flagged energy in FP64 inside the complex64 kernel, right after its own complex64 sweep,
+ * for blocks whose FP64 layout fits that kernel's shared memory and groups of at least 16
+ * lanes per resident CTA (the others take the second pass); -1 = re-sweep inside the kernel
+ * wherever the layout fits.  All give bitwise the same results. */
 typedef struct {
   int device_ordinal;
   void* stream;
@@ -105,6 +110,7 @@ typedef struct {
   int general_update;
   int chain_warps;
   int long_chain_split;
+  int mixed_two_pass;
 } negf_opts;
 
 /* Create / destroy a context on one GPU.  opts may be NULL (defaults: device 0, own

@@ -437,7 +437,8 @@ int negf_create(negf_ctx** out, const negf_opts* opts) {
   const int bw = c->opts.blk_warps, cw = c->opts.chain_warps;
   if (c->opts.precision < 0 || c->opts.precision > 2 || !(bw == -1 || bw == 0 || bw == 1 || bw == 2 || bw == 4) ||
       c->opts.blk_ctas_per_sm < 0 || !(cw == 0 || cw == 1 || cw == 2 || cw == 4 || cw == 8) ||
-      c->opts.long_chain_split < -1 || c->opts.long_chain_split > 1) {
+      c->opts.long_chain_split < -1 || c->opts.long_chain_split > 1 || c->opts.mixed_two_pass < -1 ||
+      c->opts.mixed_two_pass > 1) {
     delete c;
     return NEGF_EINVAL;
   }

@@ -196,6 +196,15 @@ struct SweepArgs {
   // slot per T slot (the integrand of the semi-adaptive grid); null when not wanted
   double* ring_cap = nullptr;
   int cap_ring = -1;
+  // mixed precision, register-tiled complex64 sweep of wide blocks: a real-axis lane whose
+  // residual exceeds flag_threshold, whose growth exceeds growth_threshold or whose energy is
+  // flagged in edge (per T slot) is re-swept in FP64 by the same CTA (FP64 shared-memory layout
+  // for fuse_bmax x fuse_mmax blocks), which sets flags[T slot] = 1
+  int fuse = 0;
+  int fuse_bmax = 0, fuse_mmax = 0;
+  double flag_threshold = 0.0, growth_threshold = 0.0;
+  const unsigned char* edge = nullptr;
+  int* flags = nullptr;
 };
 
 // ---------------------------------------------------------------- launchers

@@ -163,7 +163,7 @@ int check_ready(Ctx* c, Dev* d) {
 void free_plan_bufs(Ctx* c, PlanBufs& b) {
   for (DBuf* x : {&b.views, &b.items, &b.order, &b.counter, &b.partial, &b.tpart, &b.stage, &b.reduce, &b.status,
                   &b.resid, &b.order2, &b.growth, &b.prep, &b.hu, &b.gen, &b.genjobs, &b.genstat,
-                  &b.segitems, &b.recitem, &b.segrec})
+                  &b.segitems, &b.recitem, &b.segrec, &b.flags, &b.edge})
     c->arena.release(*x);
 }
 
@@ -226,9 +226,9 @@ static size_t blk_smem(bool f32, int b, int m, int w) {
   const int k = blk32_of(f32, b, m, w);
   return k ? blk32_smem_bytes(k) : sweep_blk_smem_bytes_t(b, m, f32 ? 8 : 16, w);
 }
-static int blk_occupancy(bool f32, int w, int b, int m) {
+static int blk_occupancy(bool f32, int w, int b, int m, bool fuse = false) {
   const int k = blk32_of(f32, b, m, w);
-  return k ? blk32_occupancy(k) : sweep_blk_occupancy_t(f32, w, b, m);
+  return k ? blk32_occupancy(k, fuse ? 1 : 0) : sweep_blk_occupancy_t(f32, w, b, m);
 }
 static int blk_launch(bool f32, const SweepArgs& a, int b, int m, int grid, int w, cudaStream_t s) {
   const int k = blk32_of(f32, b, m, w);
@@ -241,9 +241,9 @@ static long long blk_layer_bytes(bool f32, int b, int m, int w) {
   return k ? blk32_stage_layer_bytes(k) : (long long)(b * b + b * m) * 16;
 }
 
-static int blk_occ(Ctx* c, bool f32, int w, int b, int m) {
+static int blk_occ(Ctx* c, bool f32, int w, int b, int m, bool fuse = false) {
   if (blk_smem(f32, b, m, w) > 227 * 1024) return 0;
-  int occ = blk_occupancy(f32, w, b, m);
+  int occ = blk_occupancy(f32, w, b, m, fuse);
   if (c->opts.blk_ctas_per_sm > 0) occ = std::min(occ, c->opts.blk_ctas_per_sm);
   return occ;
 }
@@ -588,6 +588,25 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       tune_chain[g] = true;
   }
 
+  // mixed path: the complex64 kernel of a wide-block group re-sweeps flagged lanes in FP64 in
+  // the same CTA when the FP64 compact layout fits its shared memory and the group has enough
+  // lanes per resident CTA for those re-sweeps to overlap with complex64 lanes of other CTAs:
+  // a single-warp FP64 re-sweep takes several complex64 lane times, so a lane flagged near the
+  // end of a short group would trail the launch (measured: with 3.4 lanes per CTA the fused
+  // kernel took 1.25x the two passes).  The launch shape then follows the size policy.
+  constexpr int FUSE_LANES_PER_CTA = 16;
+  if (P.prec == NEGF_PREC_MIXED && !c->opts.mixed_two_pass)
+    for (int g = 5; g < NGROUPS; ++g) {
+      if (group_class(g) != 2 || !P.ncls[g]) continue;
+      const int w = blk_eff_width(true, P.gb[g], P.gm[g], P.gw[g]);
+      if (!blk32_of(true, P.gb[g], P.gm[g], P.gw[g]) || !blk32_can_fuse(P.gb[g], P.gm[g], w)) continue;
+      const long long slots = (long long)c->sms * blk_occ(c, true, w, P.gb[g], P.gm[g], true);
+      if (c->opts.mixed_two_pass == 0 && P.ncls[g] < FUSE_LANES_PER_CTA * slots) continue;
+      P.fuse[g] = 1;
+      P.gw[g] = w;
+      tune_g[g] = false;
+    }
+
   // launch geometry and staging per group (staging sized for FP64 elements)
   long long stage_bytes = 0;
   for (int g = 0; g < NGROUPS; ++g) {
@@ -622,7 +641,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     } else {
       const size_t sm = blk_smem(f32, P.gb[g], P.gm[g], P.gw[g]);
       if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
-      const int occ = blk_occ(c, f32, P.gw[g], P.gb[g], P.gm[g]);
+      const int occ = blk_occ(c, f32, P.gw[g], P.gb[g], P.gm[g], P.fuse[g] != 0);
       per_sm = P.gcap[g] > 0 ? std::min(occ, P.gcap[g]) : cap_rule(P.ncls[g], c->sms, occ);
       wpb = 1;   // one lane (item) per CTA
       if (tune_g[g]) {   // staging for the widest trial grid
@@ -739,6 +758,11 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
                                     !ensure(c, B.growth, sizeof(double) * std::max<long long>(tpos, 1)) ||
                                     !ensure(c, B.order2, sizeof(int) * n_items))))
     return NEGF_ENOMEM;
+  bool any_fuse = false;
+  for (int g = 0; g < NGROUPS; ++g) any_fuse = any_fuse || P.fuse[g];
+  if (any_fuse && (!ensure(c, B.flags, sizeof(int) * std::max<long long>(tpos, 1)) ||
+                   !ensure(c, B.edge, (size_t)std::max<long long>(tpos, 16))))
+    return NEGF_ENOMEM;
   std::vector<ReduceDev> rd(nd);
   for (int di = 0; di < nd; ++di) {
     Dev* d = devs[di];
@@ -847,7 +871,10 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
       cudaMemcpy(B.items.p, items.data(), sizeof(WorkItem) * n_items, cudaMemcpyHostToDevice) ||
       (!order_all.empty() &&   // split items have no place in the schedule of the sweep groups
        cudaMemcpy(B.order.p, order_all.data(), sizeof(int) * order_all.size(), cudaMemcpyHostToDevice)) ||
-      cudaMemcpy(B.reduce.p, rd.data(), sizeof(ReduceDev) * nd, cudaMemcpyHostToDevice))
+      cudaMemcpy(B.reduce.p, rd.data(), sizeof(ReduceDev) * nd, cudaMemcpyHostToDevice) ||
+      (any_fuse && (cudaMemset(B.edge.p, 0, (size_t)std::max<long long>(tpos, 16)) ||
+                    (!P.edge_flag.empty() &&
+                     cudaMemcpy(B.edge.p, P.edge_flag.data(), P.edge_flag.size(), cudaMemcpyHostToDevice)))))
     return set_err(c, NEGF_ECUDA, "upload of the launch plan failed");
   if (!P.seg.empty()) {
     // owner of every record, relative to its wave's first item
@@ -897,6 +924,16 @@ static int launch_group(Ctx* c, const Plan& P, int g, const int* order, int n, i
   const bool f32 = group_f32(g);
   SweepArgs a = group_args(P, g, order, n, resid, growth);
   if (c->profile && c->lane_stats.p) a.lane_stats = (unsigned long long*)c->lane_stats.p;
+  if (P.fuse[g] && warps <= 0) {   // (a recompute launch passes its own width: never fused)
+    const PlanBufs& B = *P.bufs;
+    a.fuse = 1;
+    a.fuse_bmax = P.gb[g];
+    a.fuse_mmax = P.gm[g];
+    a.flag_threshold = c->opts.flag_threshold;
+    a.growth_threshold = c->opts.growth_threshold > 0.0 ? c->opts.growth_threshold : HUGE_VAL;
+    a.edge = (const unsigned char*)B.edge.p;
+    a.flags = (int*)B.flags.p;
+  }
   cudaStream_t s = c->stream;
   int rc;
   if (cls == 0)
@@ -927,10 +964,22 @@ static int mixed_recompute(Ctx* c, Plan& P) {
   const double thr = c->opts.flag_threshold;
   const double gthr = c->opts.growth_threshold > 0.0 ? c->opts.growth_threshold : HUGE_VAL;   // 0: off
   P.flags.assign(P.tpos, 0);
+  bool any_fuse = false;
+  for (int g = 0; g < NGROUPS; ++g) any_fuse = any_fuse || (P.fuse[g] && P.ncls[g]);
+  std::vector<int> fused_flags;
+  if (any_fuse) {   // lanes the complex64 kernel re-swept in FP64 itself
+    fused_flags.assign(P.tpos, 0);
+    if (cudaMemcpy(fused_flags.data(), B.flags.p, sizeof(int) * P.tpos, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return set_err(c, NEGF_ECUDA, "mixed-precision flags read failed");
+  }
   std::vector<int> redo[5];
   for (int i = 0; i < P.n_items; ++i) {
     const WorkItem& W = P.items[i];
     if (W.kind != 0 || W.pad < 5) continue;
+    if (P.fuse[W.pad]) {
+      for (int e = 0; e < W.ne; ++e) P.flags[W.tout + e] = fused_flags[W.tout + e];
+      continue;
+    }
     bool any = false;
     for (int e = 0; e < W.ne; ++e) {
       const long long t = W.tout + e;
@@ -976,6 +1025,12 @@ int launch_plan(Ctx* c, Plan& P) {
   if (cudaMemsetAsync(B.counter.p, 0, sizeof(int) * 16, s) != cudaSuccess ||
       cudaMemsetAsync(B.tpart.p, 0, sizeof(double) * std::max<long long>(P.tpos, 1), s) != cudaSuccess)
     return set_err(c, NEGF_ECUDA, "counter reset failed");
+  for (int g = 0; g < NGROUPS; ++g)
+    if (P.fuse[g] && P.ncls[g]) {
+      if (cudaMemsetAsync(B.flags.p, 0, sizeof(int) * std::max<long long>(P.tpos, 1), s) != cudaSuccess)
+        return set_err(c, NEGF_ECUDA, "flag reset failed");
+      break;
+    }
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cap);
   const bool timed = c->profile && cap == cudaStreamCaptureStatusNone;

@@ -70,6 +70,7 @@ struct PlanBufs {
   DBuf prep, hu;   // layer diagonals of the 1 x 1 chains (descriptors, values)
   DBuf gen, genjobs, genstat;   // general leads: per-energy Sigma and Gamma factors, jobs, status
   DBuf segitems, recitem, segrec;   // chains split along the channel: items, record owners, records
+  DBuf flags, edge;   // mixed path: per T slot, re-swept in FP64 in the complex64 kernel; band-edge marks
 };
 
 struct ScSession;
@@ -176,6 +177,7 @@ struct Plan {
   int grid[NGROUPS] = {0}, ooff[NGROUPS] = {0}, ncls[NGROUPS] = {0};
   int gb[NGROUPS] = {0}, gm[NGROUPS] = {0}, gw[NGROUPS] = {0};   // bmax, mmax, warps of wide-block groups
   int gcap[NGROUPS] = {0};                                          // tuned resident CTAs per SM (0: rule)
+  int fuse[NGROUPS] = {0};   // mixed path: the complex64 kernel of group g re-sweeps flagged lanes in FP64
   long long stride[NGROUPS] = {0};
   long long tpos = 0;
   std::vector<unsigned char> edge_flag;   // per real energy of each device (tbase order, chain 0)

@@ -22,6 +22,7 @@
 // not depend on the tile class, so all CTA widths give the same bits.
 #include "blk32.cuh"
 #include "lead.cuh"
+#include "sweep_block_item.cuh"
 
 namespace negf {
 
@@ -425,7 +426,9 @@ struct Smem32 {
 
 }  // namespace
 
-template <int NW>
+// FUSE: re-sweep flagged real-axis lanes in FP64 in the same CTA (mixed precision; the FP64
+// compact layout of the block sweep in this CTA's shared memory)
+template <int NW, bool FUSE>
 __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
   using Cf = T32<NW>;
   constexpr int LD = Cf::LD, NT = Cf::NT, NTA = Cf::NTA, MAT = Cf::MAT;
@@ -798,14 +801,32 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
         }
       const double Tval = tid < 32 ? wsumd(tv) : 0.0;
       if (tid == 0) a.Tpart[W.tout] = Tval;
-      if (a.resid) {
+      double rs = 0.0, gr = 0.0;
+      if (a.resid || FUSE) {
         const double rn = cta_maxd<NW>((double)rnum, S.red, tid);
         const double rd = cta_maxd<NW>((double)rden, S.red, tid);
-        if (tid == 0) a.resid[W.tout] = rn / fmax(rd, 1e-300);
+        rs = rn / fmax(rd, 1e-300);
+        if (tid == 0 && a.resid) a.resid[W.tout] = rs;
       }
-      if (a.growth) {
-        const double gm = cta_maxd<NW>((double)gmax, S.red, tid);
-        if (tid == 0) a.growth[W.tout] = sqrt(gm);
+      if (a.growth || FUSE) {
+        gr = sqrt(cta_maxd<NW>((double)gmax, S.red, tid));
+        if (tid == 0 && a.growth) a.growth[W.tout] = gr;
+      }
+      if (FUSE) {
+        // the flag of the mixed path, the same on every thread (maxima are exact)
+        const bool redo = !(rs <= a.flag_threshold) || !(gr <= a.growth_threshold) || (a.edge && a.edge[W.tout]);
+        if (redo) {
+          __syncthreads();
+          if (tid == 0) a.flags[W.tout] = 1;
+          SweepArgs a64 = a;
+          a64.resid = nullptr;
+          a64.growth = nullptr;
+          a64.lane_stats = nullptr;
+          blk_item<double, NW, false, true>(a64, W, sm_b32, stage, a.fuse_bmax, a.fuse_mmax);
+          __syncthreads();
+          // the FP64 layout overwrote this CTA's matrices: restore the zero padding
+          for (int o = tid; o < (int)(sizeof(Smem32<NW>) / 4); o += NT) reinterpret_cast<float*>(&S)[o] = 0.0f;
+        }
       }
     }
     __syncthreads();
@@ -830,12 +851,18 @@ long long blk32_stage_layer_bytes(int nw) {
   return 2LL * nta * 12 * (long long)sizeof(cf);
 }
 
-template <int NW>
+bool blk32_can_fuse(int b, int m, int nw) {
+  return blk32_class(b, m, nw) == nw && sweep_blk_compact(b, m, 16, nw) &&
+         sweep_blk_smem_bytes_t(b, m, 16, nw) <= blk32_smem_bytes(nw);
+}
+
+template <int NW, bool FUSE>
 static int occ32() {
   const size_t smem = sizeof(Smem32<NW>);
-  cudaFuncSetAttribute(sweep_blk32_kernel<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(sweep_blk32_kernel<NW, FUSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_blk32_kernel<NW>, 32 * NW, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, sweep_blk32_kernel<NW, FUSE>, 32 * NW, smem) !=
+          cudaSuccess ||
       per < 1) {
     cudaGetLastError();
     per = 1;
@@ -843,16 +870,27 @@ static int occ32() {
   return per;
 }
 
-int blk32_occupancy(int nw) { return nw == 1 ? occ32<1>() : (nw == 2 ? occ32<2>() : occ32<4>()); }
+int blk32_occupancy(int nw, int fuse) {
+  if (fuse) return nw == 1 ? occ32<1, true>() : (nw == 2 ? occ32<2, true>() : occ32<4, true>());
+  return nw == 1 ? occ32<1, false>() : (nw == 2 ? occ32<2, false>() : occ32<4, false>());
+}
 
 int launch_blk32(const SweepArgs& a, int grid, int nw, cudaStream_t s) {
   // the dynamic shared memory limit was raised by the occupancy query when planning
-  if (nw == 1)
-    sweep_blk32_kernel<1><<<grid, 32, sizeof(Smem32<1>), s>>>(a);
-  else if (nw == 2)
-    sweep_blk32_kernel<2><<<grid, 64, sizeof(Smem32<2>), s>>>(a);
-  else
-    sweep_blk32_kernel<4><<<grid, 128, sizeof(Smem32<4>), s>>>(a);
+  if (a.fuse) {
+    if (nw == 1)
+      sweep_blk32_kernel<1, true><<<grid, 32, sizeof(Smem32<1>), s>>>(a);
+    else if (nw == 2)
+      sweep_blk32_kernel<2, true><<<grid, 64, sizeof(Smem32<2>), s>>>(a);
+    else
+      sweep_blk32_kernel<4, true><<<grid, 128, sizeof(Smem32<4>), s>>>(a);
+  } else if (nw == 1) {
+    sweep_blk32_kernel<1, false><<<grid, 32, sizeof(Smem32<1>), s>>>(a);
+  } else if (nw == 2) {
+    sweep_blk32_kernel<2, false><<<grid, 64, sizeof(Smem32<2>), s>>>(a);
+  } else {
+    sweep_blk32_kernel<4, false><<<grid, 128, sizeof(Smem32<4>), s>>>(a);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -26,7 +26,7 @@ class Opts(C.Structure):
                 ("precision", C.c_int), ("flag_threshold", C.c_double), ("edge_window", C.c_double),
                 ("fault_alloc_after", C.c_int), ("growth_threshold", C.c_double), ("blk_warps", C.c_int),
                 ("blk_ctas_per_sm", C.c_int), ("general_update", C.c_int), ("chain_warps", C.c_int),
-                ("long_chain_split", C.c_int)]
+                ("long_chain_split", C.c_int), ("mixed_two_pass", C.c_int)]
 
 
 class Lead(C.Structure):
@@ -261,10 +261,11 @@ class Context:
 
     def __init__(self, device=0, stream=None, hbm_budget=0, precision=PREC_FP64, flag_threshold=0.0,
                  edge_window=0.0, fault_alloc_after=0, growth_threshold=0.0, blk_warps=0, blk_ctas_per_sm=0,
-                 general_update=0, chain_warps=0, long_chain_split=0):
+                 general_update=0, chain_warps=0, long_chain_split=0, mixed_two_pass=0):
         self.lib = load()
         o = Opts(device, stream or 0, hbm_budget, precision, flag_threshold, edge_window, fault_alloc_after,
-                 growth_threshold, blk_warps, blk_ctas_per_sm, general_update, chain_warps, long_chain_split)
+                 growth_threshold, blk_warps, blk_ctas_per_sm, general_update, chain_warps, long_chain_split,
+                 mixed_two_pass)
         h = C.c_void_p()
         rc = self.lib.negf_create(C.byref(h), C.byref(o))
         if rc:

@@ -82,3 +82,25 @@ def test_mixed_flags_cover_band_edges():
     # every energy near the subband edge is flagged (its whole 32-energy item is recomputed)
     assert np.all(flags[near] == 1)
     assert np.all(resid >= 0.0)
+
+
+@pytest.mark.parametrize("n_tube,N", [(17, 24), (34, 6)])
+def test_fused_recompute_equals_two_pass(n_tube, N):
+    """The complex64 kernel re-sweeps a flagged energy in FP64 in the same CTA (blocks whose FP64
+    layout fits its shared memory): the same FP64 arithmetic as the second pass, so every output
+    and every flag is bitwise the same."""
+    from paper_2407_14633_gb300 import negf
+    from tests.cases import lib_device, lib_grid
+    p = case_params("real", N, 160, 16, synth.sinusoid_profile(N, 4), mu_D=-0.1, n_tube=n_tube, U_S=0.0, U_D=0.0)
+    out = []
+    for two_pass in (-1, 1):   # re-sweep inside the kernel wherever it fits / always a second pass
+        with ctx_with(negf.PREC_MIXED, mixed_two_pass=two_pass) as ctx:
+            dev = lib_device(ctx, "real", n_tube, p["t"], N, p["U_S"], p["U_D"])
+            ctx.set_potential(dev, p["U"])
+            lib_grid(ctx, dev, p)
+            out.append(ctx.compute_diag(dev))
+    a, b = out
+    assert np.array_equal(a["flags"], b["flags"]) and a["flags"].sum() > 0
+    for k in ("n", "T", "n_cont", "n_real"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["I"] == b["I"]
