@@ -949,9 +949,18 @@ static int launch_group(Ctx* c, const Plan& P, int g, const int* order, int n, i
   return NEGF_OK;
 }
 
+// MIXED: the FP64 group g < 5 whose lanes (the contour lanes) join the recompute launch of
+// the flagged real-axis lanes instead of a launch of their own: its complex64 partner group
+// has lanes and re-sweeps them in a second pass.  Alone, a few dozen contour lanes are a thin
+// partial wave that holds the GPU for a whole FP64 lane time.
+static bool mixed_deferred(const Plan& P, int g) {
+  return P.prec == NEGF_PREC_MIXED && g < 5 && P.ncls[g] && P.ncls[g + 5] && !P.fuse[g + 5];
+}
+
 // MIXED: read the FP32 residuals, flag real-axis lanes (sum-rule residual above the
 // threshold, or a lead band edge within the window) and re-run the items holding them in
-// FP64 into the same partial and T slots.
+// FP64 into the same partial and T slots, followed in the same launch by the deferred FP64
+// groups' lanes.
 static int mixed_recompute(Ctx* c, Plan& P) {
   const PlanBufs& B = *P.bufs;
   cudaStream_t s = c->stream;
@@ -972,10 +981,14 @@ static int mixed_recompute(Ctx* c, Plan& P) {
     if (cudaMemcpy(fused_flags.data(), B.flags.p, sizeof(int) * P.tpos, cudaMemcpyDeviceToHost) != cudaSuccess)
       return set_err(c, NEGF_ECUDA, "mixed-precision flags read failed");
   }
-  std::vector<int> redo[5];
+  std::vector<int> redo[5], late[5];
   for (int i = 0; i < P.n_items; ++i) {
     const WorkItem& W = P.items[i];
-    if (W.kind != 0 || W.pad < 5) continue;
+    if (W.pad < 5) {
+      if (mixed_deferred(P, W.pad)) late[W.pad].push_back(i);
+      continue;
+    }
+    if (W.kind != 0) continue;
     if (P.fuse[W.pad]) {
       for (int e = 0; e < W.ne; ++e) P.flags[W.tout + e] = fused_flags[W.tout + e];
       continue;
@@ -992,11 +1005,14 @@ static int mixed_recompute(Ctx* c, Plan& P) {
   }
   std::vector<int> all;
   int off[5];
+  P.recomputed = 0;
   for (int g = 0; g < 5; ++g) {
+    P.recomputed += (int)redo[g].size();
+    // the real-axis lanes (the longer sweeps) first, then the deferred contour lanes
+    redo[g].insert(redo[g].end(), late[g].begin(), late[g].end());
     off[g] = (int)all.size();
     all.insert(all.end(), redo[g].begin(), redo[g].end());
   }
-  P.recomputed = (int)all.size();
   if (all.empty()) return NEGF_OK;
   if (cudaMemcpy(B.order2.p, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemsetAsync(B.counter.p, 0, sizeof(int) * 16, s) != cudaSuccess)
@@ -1045,7 +1061,7 @@ int launch_plan(Ctx* c, Plan& P) {
     ++c->launches;
   }
   for (int g = 0; g < NGROUPS; ++g) {
-    if (!P.ncls[g]) continue;
+    if (!P.ncls[g] || mixed_deferred(P, g)) continue;
     double* resid = group_f32(g) ? (double*)B.resid.p : nullptr;
     double* growth = group_f32(g) ? (double*)B.growth.p : nullptr;
     int rc = launch_group(c, P, g, (const int*)B.order.p + P.ooff[g], P.ncls[g], P.grid[g], resid, growth);

@@ -42,7 +42,7 @@ struct T32 {
   static constexpr int NT = 32 * NW;
   static constexpr int NTA = NRT * NCT;                          // threads that own a tile
   static constexpr int MAT = PR * LD;                            // elements per matrix buffer
-  static constexpr int NBUF = 7;
+  static constexpr int NBUF = 6;
 };
 
 constexpr int B32_RED = 8;
@@ -429,7 +429,7 @@ struct Smem32 {
 // FUSE: re-sweep flagged real-axis lanes in FP64 in the same CTA (mixed precision; the FP64
 // compact layout of the block sweep in this CTA's shared memory)
 template <int NW, bool FUSE>
-__global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) sweep_blk32_kernel(SweepArgs a) {
   using Cf = T32<NW>;
   constexpr int LD = Cf::LD, NT = Cf::NT, NTA = Cf::NTA, MAT = Cf::MAT;
   extern __shared__ __align__(16) unsigned char sm_b32[];
@@ -465,10 +465,13 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
     const int mS = LS.m, mD = LDv.m;
     double* part = a.partial + W.part;
     const int kmax = C.kmax;
-    const long long lstride = (real ? 2 : 1) * TILEB;
-    // staging of layer l: the gL_l tile chunks, then (real-axis lanes) the R_l tile chunks
-    auto gl_of = [&](int l) { return reinterpret_cast<float4*>(stage + (long long)l * lstride); };
-    auto rl_of = [&](int l) { return reinterpret_cast<float4*>(stage + (long long)l * lstride) + 6 * NTA; };
+    const long long lstride = (real ? 3 : 1) * TILEB;
+    // staging of layer l: the y_l tile chunks, then (real-axis lanes) the gL_l and R_l tile
+    // chunks.  The backward sweep reads y_l back instead of forming it again from gL_{l-1};
+    // only the real-axis lanes need gL_l there (for K_l).
+    auto yl_of = [&](int l) { return reinterpret_cast<float4*>(stage + (long long)l * lstride); };
+    auto gl_of = [&](int l) { return reinterpret_cast<float4*>(stage + (long long)l * lstride) + 6 * NTA; };
+    auto rl_of = [&](int l) { return reinterpret_cast<float4*>(stage + (long long)l * lstride) + 12 * NTA; };
 
     cd eps;
     double wS = 0.0, wD = 0.0;
@@ -543,17 +546,16 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
     }
     __syncthreads();
 
-    // buffers (rotated by pointer): P/G, T1, GL, GLm, GR, K, R
-    cf* bG = S.mat[0];
-    cf* bT = S.mat[1];
-    cf* bGL = S.mat[2];
-    cf* bGLm = S.mat[3];
-    cf* bGR = S.mat[4];
-    cf* const bK = S.mat[5];
-    cf* const bR = S.mat[6];
+    // buffers: P/G, T1, GL, GR, K, R
+    cf* const bG = S.mat[0];
+    cf* const bT = S.mat[1];
+    cf* const bGL = S.mat[2];
+    cf* const bGR = S.mat[3];
+    cf* const bK = S.mat[4];
+    cf* const bR = S.mat[5];
     float gmax = 0.0f;   // largest |gL_l entry|^2 seen by this thread (growth diagnostic)
 
-    // ---- forward sweep: gL_l into bG (logical), staged with R_l
+    // ---- forward sweep: gL_l into bG (logical), staged with y_l and R_l
     Tile ta, tr_;
     if (real) {
       // R_0 = L_S: rows at the lead sites, zeros elsewhere
@@ -582,6 +584,7 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
         if (act) {
           tzero(ta);
           tcol<LD, false>(ta, bT, ccnt, cidx, cval, kmax, b, r0, c0);   // y_l = X H_{l-1,l}
+          gstore<NTA>(yl_of(l), tid, ta);
           talpha(ta, l, L, b, rpb, spr, eps, S.ip, S.sigS, S.sigD, S.sinvS, S.sinvD, r0, c0);
           if (real) tgemm<LD>(tr_, bT, bR, b, r0, c0);                   // R_l = X R_{l-1}
         }
@@ -607,7 +610,7 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
       }
       tinv<NW, 1>(ta, ta, bG, nullptr, b, S.inv, tid, act, tc, r0, c0);   // gL_l = (alpha_l - y_l)^{-1}
       bar<NW>();
-      if (act) {   // stage gL_l (logical tile) and track its largest entry
+      if (act) {   // stage gL_l (logical tile, real-axis lanes) and track its largest entry
         Tile tg;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -616,7 +619,7 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
             tg.v[i][j] = bG[(r0 + i) * LD + pcol(c0 + j)];
             if (a.growth) gmax = fmaxf(gmax, fmaf(tg.v[i][j].re, tg.v[i][j].re, tg.v[i][j].im * tg.v[i][j].im));
           }
-        gstore<NTA>(gl_of(l), tid, tg);
+        if (real && l < L - 1) gstore<NTA>(gl_of(l), tid, tg);
       }
     }
     if (a.lane_stats && tid == 0) atomicAdd(a.lane_stats + (real ? 1 : 3), 1ull);
@@ -649,9 +652,11 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
       if (act) {
         tzero(ta);
         talpha(ta, L - 1, L, b, rpb, spr, eps, S.ip, S.sigS, S.sigD, S.sinvS, S.sinvD, r0, c0);
-        Tile tg;
-        gload<NTA>(tg, gl_of(L - 2), tid);
-        tstore<LD>(bGL, tg, r0, c0);
+        if (real) {
+          Tile tg;
+          gload<NTA>(tg, gl_of(L - 2), tid);
+          tstore<LD>(bGL, tg, r0, c0);
+        }
       }
       tinv<NW, 1>(ta, ta, bGR, nullptr, b, S.inv, tid, act, tc, r0, c0);  // gR_{L-1} = alpha_{L-1}^{-1}
     }
@@ -668,12 +673,8 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
         const int* cidx = S.ip.cs_idx + (long long)l * b * kmax;
         const cf* cval = S.ip.cs_val + (long long)l * b * kmax;
         if (act) {
-          Tile tg;
-          if (l > 0) {   // gL_{l-1} for y_l (and next layer's gL)
-            gload<NTA>(tg, gl_of(l - 1), tid);
-            tstore<LD>(bGLm, tg, r0, c0);
-          }
           if (real) {    // R_l
+            Tile tg;
             gload<NTA>(tg, rl_of(l), tid);
             tstore<LD>(bR, tg, r0, c0);
           }
@@ -689,43 +690,31 @@ __global__ void __launch_bounds__(32 * NW) sweep_blk32_kernel(SweepArgs a) {
         bar<NW>();
         Tile tk, tm1;
         if (act) {
-          if (real) tgemm<LD>(tk, bG, bK, b, r0, c0);                          // K_l = Wk K_{l+1}
+          if (real) {
+            tgemm<LD>(tk, bG, bK, b, r0, c0);                                  // K_l = Wk K_{l+1}
+            if (l > 0) {   // gL_{l-1}, the next layer's gL (bGL was last read by Wk)
+              Tile tg;
+              gload<NTA>(tg, gl_of(l - 1), tid);
+              tstore<LD>(bGL, tg, r0, c0);
+            }
+          }
           tzero(tm1);
           tcol<LD, true>(tm1, bT, rcnt, ridx, rval, kmax, b, r0, c0);          // x_l = W1 H_{l+1,l}
           talpha(tm1, l, L, b, rpb, spr, eps, S.ip, S.sigS, S.sigD, S.sinvS, S.sinvD, r0, c0);
         }
         bar<NW>();
-        if (act) {
-          if (real) tstore<LD>(bK, tk, r0, c0);
-          if (l > 0) {
-            const int* pcnt = S.ip.cs_cnt + (long long)(l - 1) * b;
-            const int* pidx = S.ip.cs_idx + (long long)(l - 1) * b * kmax;
-            const cf* pval = S.ip.cs_val + (long long)(l - 1) * b * kmax;
-            tzero(ta);
-            trow<LD, true>(ta, pcnt, pidx, pval, kmax, bGLm, b, r0, c0);       // H_{l,l-1} gL_{l-1}
-            tstore<LD>(bT, ta, r0, c0);
-          }
-        }
+        if (act && real) tstore<LD>(bK, tk, r0, c0);
         if (l > 0) {
-          bar<NW>();
-          if (act) {
-            const int* pcnt = S.ip.cs_cnt + (long long)(l - 1) * b;
-            const int* pidx = S.ip.cs_idx + (long long)(l - 1) * b * kmax;
-            const cf* pval = S.ip.cs_val + (long long)(l - 1) * b * kmax;
-            tzero(ta);
-            tcol<LD, false>(ta, bT, pcnt, pidx, pval, kmax, b, r0, c0);        // y_l
+          if (act) {   // y_l as the forward sweep formed it
+            gload<NTA>(ta, yl_of(l), tid);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
               for (int j = 0; j < 4; ++j) ta.v[i][j] = tm1.v[i][j] - ta.v[i][j];   // alpha_l - x_l - y_l
           }
-          // G_ll = (alpha_l - x_l - y_l)^{-1} into bG, gR_l = (alpha_l - x_l)^{-1} into bGLm's
-          // partner: results go to bG (free since K_l was formed) and bGR (gR_{l+1} was used by W1)
+          // G_ll = (alpha_l - x_l - y_l)^{-1} into bG (free since K_l was formed), gR_l =
+          // (alpha_l - x_l)^{-1} into bGR (gR_{l+1} was last read by W1)
           tinv<NW, 2>(ta, tm1, bG, bGR, b, S.inv, tid, act, tc, r0, c0);
-          // rotate: gL_{l-1} becomes the next layer's gL_l; gL_l's buffer is free
-          cf* oGL = bGL;
-          bGL = bGLm;
-          bGLm = oGL;
         } else {
           tinv<NW, 1>(tm1, tm1, bG, nullptr, b, S.inv, tid, act, tc, r0, c0);   // G_00 = (alpha_0 - x_0)^{-1}
         }
@@ -848,7 +837,7 @@ size_t blk32_smem_bytes(int nw) {
 
 long long blk32_stage_layer_bytes(int nw) {
   const int nta = nw == 1 ? T32<1>::NTA : (nw == 2 ? T32<2>::NTA : T32<4>::NTA);
-  return 2LL * nta * 12 * (long long)sizeof(cf);
+  return 3LL * nta * 12 * (long long)sizeof(cf);   // y_l, gL_l, R_l
 }
 
 bool blk32_can_fuse(int b, int m, int nw) {
