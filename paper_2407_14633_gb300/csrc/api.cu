@@ -1,6 +1,7 @@
 // C ABI of libnegf: contexts, device arena, devices, nanotube builders, leads, grids.
 // The NEGF evaluation itself is in compute.cu, the self-consistent loop in sc.cu and the
 // serving scheduler in serve.cu.
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -157,6 +158,15 @@ int upload_chain(Ctx* c, Dev* d, ChainData& ch) {
       }
   for (size_t i = 1; i < ch.Hup.size() && ch.h_sym; i += 2)
     if (ch.Hup[i] != 0.0) ch.h_sym = false;
+  // uniform layers (a tube of one ring type): the block sweeps read layer 0's blocks only
+  const size_t bb2 = 2 * (size_t)b * b;
+  bool hd_uniform = true, cp_uniform = true;
+  for (int l = 1; l < L && hd_uniform; ++l)
+    hd_uniform = std::equal(ch.Hdiag.begin() + l * bb2, ch.Hdiag.begin() + (l + 1) * bb2, ch.Hdiag.begin());
+  for (int l = 1; l < L - 1 && cp_uniform; ++l)
+    cp_uniform = std::equal(ch.Hup.begin() + l * bb2, ch.Hup.begin() + (l + 1) * bb2, ch.Hup.begin());
+  ch.hd_step = hd_uniform ? 0 : b * b;
+  ch.cp_step = cp_uniform ? 0 : b;
   if ((rc = upload(c, ch.dHdiag, ch.Hdiag.data(), ch.Hdiag.size() * 8))) return rc;
   if ((rc = upload_f32(c, ch.dHdiag_f, ch.Hdiag))) return rc;
   if ((rc = upload(c, ch.dHup, ch.Hup.data(), std::max<size_t>(ch.Hup.size(), 2) * 8))) return rc;

@@ -133,6 +133,10 @@ struct ChainView {
   const int* cs_idx;
   const cd* cs_val;
   int kmax;
+  // elements between consecutive layers of Hdiag (b*b) and of the sparse forms' count arrays
+  // (b; kmax times that for idx and val); 0 when every layer holds the same block, so that
+  // the block sweeps read one L1-resident copy (the arrays still hold every layer)
+  int hd_step, cp_step;
   const cf* Hdiag_f;  // complex64 copies of Hdiag, cs_val, rs_val (complex64 sweeps)
   const cf* cs_val_f;
   const cf* rs_val_f;

@@ -113,6 +113,8 @@ DeviceView make_view(Ctx* c, Dev* d, const ViewOverride* o) {
     cv.rs_idx = (const int*)ch.drs_idx.p;
     cv.rs_val = (const cd*)ch.drs_val.p;
     cv.kmax = ch.kmax;
+    cv.hd_step = ch.hd_step;
+    cv.cp_step = ch.cp_step;
     cv.Hdiag_f = (const cf*)ch.dHdiag_f.p;
     cv.cs_val_f = (const cf*)ch.dcs_val_f.p;
     cv.rs_val_f = (const cf*)ch.drs_val_f.p;

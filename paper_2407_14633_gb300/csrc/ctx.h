@@ -57,6 +57,7 @@ struct ChainData {
   DBuf dHdiag, dHup, dcs_cnt, dcs_idx, dcs_val, drs_cnt, drs_idx, drs_val, dhsq;
   DBuf dHdiag_f, dcs_val_f, drs_val_f, dhsq_f;   // FP32 copies for the complex64 sweeps
   bool diag_real = false;                        // Im H_ll = 0 everywhere
+  int hd_step = 0, cp_step = 0;                  // layer steps of Hdiag and the sparse forms (0: uniform)
   DBuf da1[2], da2[2], dat[2], dsites[2], dtw[2];
   DBuf dgen[2];   // general leads: the five m x m blocks on the device
   int kmax = 0;

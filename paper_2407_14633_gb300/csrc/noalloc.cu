@@ -176,6 +176,8 @@ extern "C" int negf_chain1_compute_noalloc(void* stream, int n_rings, const doub
   v.c = reinterpret_cast<const cd*>(c);
   ChainView& cv = v.ch[0];
   cv.Hdiag = reinterpret_cast<const cd*>(Hdiag);
+  cv.hd_step = 1;
+  cv.cp_step = 1;
   cv.hsq = n_rings > 1 ? hsq : U;   // never read when there is one ring
   cv.g_b = g_b;
   const double* ld = reinterpret_cast<const double*>(base + lo.lead);

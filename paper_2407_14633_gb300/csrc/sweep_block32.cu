@@ -13,8 +13,12 @@
 //     place.  The pivot search packs |v|^2 and the row index into one 32-bit key for a single
 //     warp max-reduction.  The two inverses of a backward step run interleaved, sharing their
 //     barriers;
-//   - gL_l and R_l are staged to global memory in tile order (each thread writes and later
-//     reads its own 96 contiguous bytes).
+//   - y_l, gL_l and R_l are staged to global memory in tile order (each thread writes and
+//     later reads its own six 16-byte chunks); the backward sweep reads y_l back rather than
+//     forming it again, which saves a matrix buffer (10 one-warp CTAs per SM) and two sparse
+//     products per layer;
+//   - a tube whose layers all hold the same blocks reads layer 0's H_ll and couplings for
+//     every layer (an L1-resident copy).
 // Tile classes (CTA width): 1 warp for b <= 18 (6 x 5 tiles), 2 warps for b <= 27 (9 x 7), 4
 // warps for b <= 36 (12 x 9); wider blocks keep the shared-memory kernel.  Matrices are kept
 // with exact zero padding outside b x b, so padded rows and columns never feed a result.
@@ -133,12 +137,43 @@ __device__ __forceinline__ void gload(Tile& x, const float4* g, int t) {
 }
 
 // out[r][c] += sum_e s(val[r][e]) M[idx[r][e]][c]  (rows r < b; s = conj when CJ).  Every
-// row holds kmax slots (unused ones index 0 with value 0); the slot loads are issued for all
-// kmax slots at once and the count only predicates the multiply-adds, so the count's load is
-// not on the path to the operands.
+// row holds kmax slots (unused ones index 0 with value 0); the count only predicates the
+// multiply-adds.  Up to KS slots per row (the (n,0) tubes have 2) run unrolled, every slot
+// load of the three rows issued before the first operand load; wider couplings loop.
+constexpr int KS = 2;
 template <int LD, bool CJ>
 __device__ __forceinline__ void trow(Tile& t, const int* cnt, const int* idx, const cf* val, int kmax, const cf* M,
                                      int b, int r0, int c0) {
+  if (kmax <= KS) {
+    int n[3], q[3][KS];
+    cf v[3][KS];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int r = r0 + i;
+      const int rr = r < b ? r : 0;
+      n[i] = r < b ? cnt[rr] : 0;
+#pragma unroll
+      for (int e = 0; e < KS; ++e) {
+        const bool in = e < kmax;
+        v[i][e] = in ? val[rr * kmax + e] : mk(0.0f, 0.0f);
+        q[i][e] = in ? idx[rr * kmax + e] : 0;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int e = 0; e < KS; ++e)
+        if (e < n[i]) {
+          const cf* m = M + q[i][e] * LD + pcol(c0);
+          const float4 p = *reinterpret_cast<const float4*>(m);
+          const float4 u = *reinterpret_cast<const float4*>(m + 2);
+          const cf y[4] = {mk(p.x, p.y), mk(p.z, p.w), mk(u.x, u.y), mk(u.z, u.w)};
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            t.v[i][j] = CJ ? cmac_cj(t.v[i][j], v[i][e], y[j]) : cmac(t.v[i][j], v[i][e], y[j]);
+        }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const int r = r0 + i;
@@ -164,6 +199,34 @@ __device__ __forceinline__ void trow(Tile& t, const int* cnt, const int* idx, co
 template <int LD, bool CJ>
 __device__ __forceinline__ void tcol(Tile& t, const cf* M, const int* cnt, const int* idx, const cf* val, int kmax,
                                      int b, int r0, int c0) {
+  if (kmax <= KS) {
+    int n[4], q[4][KS];
+    cf v[4][KS];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + j;
+      const int cc = c < b ? c : 0;
+      n[j] = c < b ? cnt[cc] : 0;
+#pragma unroll
+      for (int e = 0; e < KS; ++e) {
+        const bool in = e < kmax;
+        v[j][e] = in ? val[cc * kmax + e] : mk(0.0f, 0.0f);
+        q[j][e] = pcol(in ? idx[cc * kmax + e] : 0);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < KS; ++e)
+        if (e < n[j]) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const cf x = M[(r0 + i) * LD + q[j][e]];
+            t.v[i][j] = CJ ? cmac_cj(t.v[i][j], v[j][e], x) : cmac(t.v[i][j], x, v[j][e]);
+          }
+        }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = c0 + j;
@@ -197,7 +260,9 @@ struct ItemPtrs {
   const int* rs_cnt;
   const int* rs_idx;
   const cf* rs_val;
-  int kmax, mS, mD, pad;
+  int kmax, mS, mD;
+  int hd_step, cp_step;   // layer steps of hd and of the sparse forms (0: every layer the same)
+  int pad;
 };
 
 // In place: t := alpha_l - t on r, c < b (0 elsewhere), alpha_l = eps I - H_ll - U_ring -
@@ -207,7 +272,7 @@ struct ItemPtrs {
 __device__ __forceinline__ void talpha(Tile& t, int l, int L, int b, int rpb, int spr, cd eps, const ItemPtrs& P,
                                        const cd* sigS, const cd* sigD, const int* sinvS, const int* sinvD, int r0,
                                        int c0) {
-  const cf* hd = P.hd + (long long)l * b * b;
+  const cf* hd = P.hd + (long long)l * P.hd_step;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const int r = r0 + i;
@@ -501,6 +566,8 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
       q.kmax = kmax;
       q.mS = mS;
       q.mD = mD;
+      q.hd_step = C.hd_step;
+      q.cp_step = C.cp_step;
       q.pad = 0;
       S.ip = q;
     }
@@ -572,9 +639,10 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
     }
     for (int l = 0; l < L; ++l) {
       if (l > 0) {
-        const int* ccnt = S.ip.cs_cnt + (long long)(l - 1) * b;
-        const int* cidx = S.ip.cs_idx + (long long)(l - 1) * b * kmax;
-        const cf* cval = S.ip.cs_val + (long long)(l - 1) * b * kmax;
+        const long long cp = (long long)(l - 1) * S.ip.cp_step;
+        const int* ccnt = S.ip.cs_cnt + cp;
+        const int* cidx = S.ip.cs_idx + cp * kmax;
+        const cf* cval = S.ip.cs_val + cp * kmax;
         if (act) {   // X = H_{l,l-1} gL_{l-1} = Hup_{l-1}^dagger gL_{l-1}
           tzero(ta);
           trow<LD, true>(ta, ccnt, cidx, cval, kmax, bG, b, r0, c0);
@@ -666,12 +734,13 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
     for (int l = L - 1; l >= 0; --l) {
       if (l < L - 1) {
         // entering: bG and bT free, bGR = gR_{l+1}, bK = K_{l+1}, bGL = gL_l
-        const int* rcnt = S.ip.rs_cnt + (long long)l * b;
-        const int* ridx = S.ip.rs_idx + (long long)l * b * kmax;
-        const cf* rval = S.ip.rs_val + (long long)l * b * kmax;
-        const int* ccnt = S.ip.cs_cnt + (long long)l * b;
-        const int* cidx = S.ip.cs_idx + (long long)l * b * kmax;
-        const cf* cval = S.ip.cs_val + (long long)l * b * kmax;
+        const long long cp = (long long)l * S.ip.cp_step;
+        const int* rcnt = S.ip.rs_cnt + cp;
+        const int* ridx = S.ip.rs_idx + cp * kmax;
+        const cf* rval = S.ip.rs_val + cp * kmax;
+        const int* ccnt = S.ip.cs_cnt + cp;
+        const int* cidx = S.ip.cs_idx + cp * kmax;
+        const cf* cval = S.ip.cs_val + cp * kmax;
         if (act) {
           if (real) {    // R_l
             Tile tg;

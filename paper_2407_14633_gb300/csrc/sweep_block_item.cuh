@@ -514,7 +514,7 @@ __device__ __forceinline__ void alpha_minus(cx<T>* out, const cx<T>* Sub, int l,
                                             cd eps, const DeviceView& D, const ChainView& C, const cd* sigS,
                                             const cd* sigD, int eidx, int tid) {
   constexpr int NT = 32 * NW;
-  const cx<T>* hd = hdiag_t<T>(C) + (long long)l * b * b;
+  const cx<T>* hd = hdiag_t<T>(C) + (long long)l * C.hd_step;
   const int nn = b * b;
   for (int o = tid; o < nn; o += NT) out[o] = Sub ? mk(-hd[o].re - Sub[o].re, -hd[o].im - Sub[o].im) : mk(-hd[o].re, -hd[o].im);
   csync<NW>();
@@ -638,9 +638,9 @@ __device__ __forceinline__ void blk_item(const SweepArgs a, const WorkItem& W, u
   float gdg = 0.0f;
   for (int l = 0; l < L; ++l) {
     if (l > 0) {
-      const int* ccnt = C.cs_cnt + (long long)(l - 1) * b;
-      const int* cidx = C.cs_idx + (long long)(l - 1) * b * kmax;
-      const cx<T>* cval = csval_t<T>(C) + (long long)(l - 1) * b * kmax;
+      const int* ccnt = C.cs_cnt + (long long)(l - 1) * C.cp_step;
+      const int* cidx = C.cs_idx + (long long)(l - 1) * C.cp_step * kmax;
+      const cx<T>* cval = csval_t<T>(C) + (long long)(l - 1) * C.cp_step * kmax;
       hdn_times<T, NT>(X, P, b, b, b, ccnt, cidx, cval, kmax, tid);            // X = H_{l,l-1} gL_{l-1}
       csync<NW>();
       times_hup<T, NT>(A, X, b, b, ccnt, cidx, cval, kmax, tid);               // y_l = X H_{l-1,l}
@@ -758,9 +758,9 @@ __device__ __forceinline__ void blk_item(const SweepArgs a, const WorkItem& W, u
   for (int l = L - 1; l >= 0; --l) {
     if (l < L - 1) {
       const cx<T>* sg = reinterpret_cast<const cx<T>*>(stage + (long long)l * lstride);
-      const int* ccnt = C.cs_cnt + (long long)l * b;
-      const int* cidx = C.cs_idx + (long long)l * b * kmax;
-      const cx<T>* cval = csval_t<T>(C) + (long long)l * b * kmax;
+      const int* ccnt = C.cs_cnt + (long long)l * C.cp_step;
+      const int* cidx = C.cs_idx + (long long)l * C.cp_step * kmax;
+      const cx<T>* cval = csval_t<T>(C) + (long long)l * C.cp_step * kmax;
       if (!TWO) {
         for (int o = tid; o < nn; o += NT) Gl[o] = sg[o];
         if (real && !CMP)
@@ -816,9 +816,9 @@ __device__ __forceinline__ void blk_item(const SweepArgs a, const WorkItem& W, u
         cx<T>* Wk = Gl;
         cx<T>* W1 = Z;
         cx<T>* Gr = Wm;
-        const int* rcnt = C.rs_cnt + (long long)l * b;
-        const int* ridx = C.rs_idx + (long long)l * b * kmax;
-        const cx<T>* rval = rsval_t<T>(C) + (long long)l * b * kmax;
+        const int* rcnt = C.rs_cnt + (long long)l * C.cp_step;
+        const int* ridx = C.rs_idx + (long long)l * C.cp_step * kmax;
+        const cx<T>* rval = rsval_t<T>(C) + (long long)l * C.cp_step * kmax;
         if (real)
           for (int o = tid; o < b * mS; o += NT) Rl[o] = sg[bb + o];
         if (l > 0) {
@@ -833,9 +833,9 @@ __device__ __forceinline__ void blk_item(const SweepArgs a, const WorkItem& W, u
         csync<NW>();
         alpha_minus<T, NW>(Gr, G, l, L, b, rpb, spr, eps, D, C, sigS, sigD, eidx, tid);  // alpha_l - x_l
         if (l > 0) {
-          const int* pcnt = C.cs_cnt + (long long)(l - 1) * b;
-          const int* pidx = C.cs_idx + (long long)(l - 1) * b * kmax;
-          const cx<T>* pval = csval_t<T>(C) + (long long)(l - 1) * b * kmax;
+          const int* pcnt = C.cs_cnt + (long long)(l - 1) * C.cp_step;
+          const int* pidx = C.cs_idx + (long long)(l - 1) * C.cp_step * kmax;
+          const cx<T>* pval = csval_t<T>(C) + (long long)(l - 1) * C.cp_step * kmax;
           hdn_times<T, NT>(W1, GpB, b, b, b, pcnt, pidx, pval, kmax, tid);          // H_{l,l-1} gL_{l-1}
           csync<NW>();
           times_hup<T, NT>(Wk, W1, b, b, pcnt, pidx, pval, kmax, tid);              // y_l

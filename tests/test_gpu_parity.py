@@ -95,6 +95,35 @@ def test_flux_threaded_tube_general_blocks(n_tube, N, blk_warps):
     check(p, r, o)
 
 
+@pytest.mark.parametrize("n_tube,N,blk_warps,prec,tol", [(17, 9, 1, "fp64", TOL), (26, 5, 2, "fp64", TOL),
+                                                         (17, 9, 1, "fp32", 1e-3), (26, 5, 2, "fp32", 1e-3)])
+def test_layer_dependent_blocks(n_tube, N, blk_warps, prec, tol):
+    """Every layer its own blocks: on-site disorder per ring, coupling strengths per layer and
+    one missing ring-to-ring bond, so that no two layers share H_ll or H_{l,l+1} and the
+    sparse forms' counts differ between layers.  A uniform tube's sweeps read layer 0's blocks
+    for every layer; this one must index each layer (FP64 to 1e-10, the complex64 sweep to
+    its plain-precision bound)."""
+    from paper_2407_14633_gb300 import negf
+    rng = np.random.default_rng(11)
+    U = synth.sinusoid_profile(N, 6)
+    p = case_params("real", N, 41, 9, U, mu_D=-0.3, n_tube=n_tube, U_S=0.0, U_D=-0.3)
+    dev_o = omdl.cnt_build("real", n_tube, p["t"], N, p["U_S"], p["U_D"])
+    ch = dev_o.chains[0]
+    ch.Hdiag = ch.Hdiag + np.einsum("lr,rs->lrs", rng.uniform(-0.2, 0.2, (N, n_tube)), np.eye(n_tube))
+    ch.Hup = ch.Hup * rng.uniform(0.9, 1.1, (N - 1, 1, 1))
+    r0, c0 = np.argwhere(ch.Hup[N // 2] != 0)[0]
+    ch.Hup[N // 2, r0, c0] = 0.0
+    o = ochg.negf_evaluate(dev_o, U, ogr_grid(p), chunk=16)
+    precision = negf.PREC_FP64 if prec == "fp64" else negf.PREC_FP32
+    with negf.Context(blk_warps=blk_warps, precision=precision) as c2:
+        dev = lib_device(c2, "real", n_tube, p["t"], N, p["U_S"], p["U_D"])
+        c2.set_hamiltonian(dev, 0, ch.Hdiag.reshape(-1).astype(complex), ch.Hup.reshape(-1).astype(complex), 1.0)
+        c2.set_potential(dev, U)
+        lib_grid(c2, dev, p)
+        r = c2.compute([dev])[0]
+    check(p, r, o, tol=tol)
+
+
 @pytest.mark.parametrize("N,n_real", [(64, 96), (192, 512)])
 def test_symmetric_update_with_bound_states(N, n_real):
     """A potential well deep enough to hold states in the gap: lanes near those states have a
