@@ -136,6 +136,17 @@ __device__ __forceinline__ void gload(Tile& x, const float4* g, int t) {
   }
 }
 
+// L2 prefetch of a staged tile (bytes from g) ahead of its gload: one line per thread
+template <int NT>
+__device__ __forceinline__ void gprefetch(const float4* g, long long bytes, int tid) {
+  const char* p = reinterpret_cast<const char*>(g);
+  const int nl = (int)((bytes + 127) / 128) + 1;   // lines a range of this length can touch
+  for (int o = tid; o < nl; o += NT) {
+    const long long off = (long long)o * 128 < bytes - 16 ? (long long)o * 128 : bytes - 16;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + off));
+  }
+}
+
 // out[r][c] += sum_e s(val[r][e]) M[idx[r][e]][c]  (rows r < b; s = conj when CJ).  Every
 // row holds kmax slots (unused ones index 0 with value 0); the count only predicates the
 // multiply-adds.  Up to KS slots per row (the (n,0) tubes have 2) run unrolled, every slot
@@ -732,6 +743,10 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
 
     float rnum = 0.0f, rden = 0.0f;   // sum-rule residual: max(0, A_S + A_D + 2 Im G) / max |2 Im G|
     for (int l = L - 1; l >= 0; --l) {
+      // the next layer's staged tiles (y_{l-1}, gL_{l-2}, R_{l-1}) on their way to L2
+      if (l >= 2) gprefetch<NT>(yl_of(l - 1), TILEB, tid);
+      if (real && l >= 2) gprefetch<NT>(gl_of(l - 2), TILEB, tid);
+      if (real && l >= 1) gprefetch<NT>(rl_of(l - 1), TILEB, tid);
       if (l < L - 1) {
         // entering: bG and bT free, bGR = gR_{l+1}, bK = K_{l+1}, bGL = gL_l
         const long long cp = (long long)l * S.ip.cp_step;
