@@ -319,46 +319,45 @@ __device__ __forceinline__ void talpha(Tile& t, int l, int L, int b, int rpb, in
 }
 
 // Scratch of the inverses: per matrix and step parity the pivot column and the pivot row,
-// and the pivot order.
+// the pivot order and each row's deferred scale (1 / its pivot).
 template <int NW>
 struct InvBuf {
   cf colb[2][2][T32<NW>::PR];
   cf rowb[2][2][T32<NW>::LD];
+  cf vs[2][T32<NW>::BMAX];
   unsigned char piv[2][64];
   unsigned char qinv[2][64];
 };
 
-// One Gauss-Jordan step on a register tile (column k is column jj of tile column kt): the
-// column multipliers f (row p's set to 0), the pivot row scaled by ip (its column k set to ip),
-// column k of the tile cleared before the rank-one update, row p replaced by the scaled row.
+// One Gauss-Jordan step on a register tile (column k is column jj of tile column kt), with
+// the pivot row's scaling deferred: every row other than p takes A[i][j] - (A[i][k] / A[p][k])
+// A[p][j] (column k: -A[i][k] / A[p][k], from a cleared column and a unit pivot-row entry);
+// row p keeps its values and gets 1 in column k, i.e. it holds A[p][k] times its scaled row,
+// which every later step treats linearly; the inverse's final store multiplies it by
+// 1 / A[p][k].
 template <int LD>
 __device__ __forceinline__ void gj_update(Tile& t, const cf* colb, const cf* rowb, cf ip, int p, int jj, bool own,
                                           int r0, int c0) {
   cf f[3], rs[4];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) f[i] = (r0 + i == p) ? mk(0.0f, 0.0f) : colb[r0 + i];
+  for (int i = 0; i < 3; ++i) f[i] = (r0 + i == p) ? mk(0.0f, 0.0f) : colb[r0 + i] * ip;
   const float4 u = *reinterpret_cast<const float4*>(rowb + pcol(c0));
   const float4 w = *reinterpret_cast<const float4*>(rowb + pcol(c0) + 2);
-  rs[0] = mk(u.x, u.y) * ip;
-  rs[1] = mk(u.z, u.w) * ip;
-  rs[2] = mk(w.x, w.y) * ip;
-  rs[3] = mk(w.z, w.w) * ip;
+  rs[0] = mk(u.x, u.y);
+  rs[1] = mk(u.z, u.w);
+  rs[2] = mk(w.x, w.y);
+  rs[3] = mk(w.z, w.w);
 #pragma unroll
   for (int j = 0; j < 4; ++j)
     if (own && j == jj) {
-      rs[j] = ip;
+      rs[j] = mk(1.0f, 0.0f);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) t.v[i][j] = mk(0.0f, 0.0f);
+      for (int i = 0; i < 3; ++i) t.v[i][j] = mk(r0 + i == p ? 1.0f : 0.0f, 0.0f);
     }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) t.v[i][j] = cmsub(t.v[i][j], f[i], rs[j]);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-    if (r0 + i == p)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) t.v[i][j] = rs[j];
 }
 
 // Pivot of column k (values in colb, rows < b): the unused row of largest |v| (magnitudes
@@ -384,11 +383,11 @@ __device__ __forceinline__ int gj_pivot(const cf* colb, int b, unsigned long lon
 // Gauss-Jordan inverses of NM (1 or 2) b x b matrices held as register tiles (t0, t1; exact
 // zeros outside b x b), implicit partial pivoting.  Step k: the owners of column k publish it;
 // every warp finds the pivot p (the unused row of largest |A[p][k]|); the owners of row p
-// publish it; every thread then updates its tile: row p becomes A[p][j] / A[p][k] with
-// A[p][k] := 1 / A[p][k], column k of every other row is cleared, and every other element
-// takes A[i][j] - A[i][k]_old * A[p][j]_new, which leaves -A[i][k]_old / A[p][k] in column
-// k.  After b steps physical (i, j) holds inv[q(i)][piv(j)], q the step of row i; D0, D1
-// receive the inverses in place of their rows and columns (zeros outside b x b).  Pivot
+// publish it; every thread then updates its tile (gj_update: row p stays, scaled by A[p][k]
+// until the end, with 1 in column k; every other row takes A[i][j] - A[i][k] A[p][j] / A[p][k],
+// column k -A[i][k] / A[p][k]).  After b steps physical (i, j) holds inv[q(i)][piv(j)] times
+// the pivot of row i, q the step of row i; D0, D1 receive the inverses, rows rescaled, in
+// place of their rows and columns (zeros outside b x b).  Pivot
 // columns and rows alternate between two buffers, so a step's writes never meet a slower
 // warp's reads of the step before.  The caller synchronises before reading D0, D1.
 template <int NW, int NM>
@@ -436,9 +435,11 @@ __device__ __forceinline__ void tinv(Tile& t0, Tile& t1, cf* D0, cf* D1, int b, 
         if (tid == 0) {
           W.piv[0][k] = (unsigned char)p0;
           W.qinv[0][p0] = (unsigned char)k;
+          W.vs[0][p0] = ip0;
           if (NM > 1) {
             W.piv[1][k] = (unsigned char)p1;
             W.qinv[1][p1] = (unsigned char)k;
+            W.vs[1][p1] = ip1;
           }
         }
         bar<NW>();
@@ -449,23 +450,28 @@ __device__ __forceinline__ void tinv(Tile& t0, Tile& t1, cf* D0, cf* D1, int b, 
       }
     }
   }
-  bar<NW>();   // the pivot order of the last step
-  // permuted stores: physical (r, c) -> inverse (q(r), piv(c)); padding stays zero
+  bar<NW>();   // the pivot order and scales of the last step
+  // permuted stores: physical (r, c) -> inverse (q(r), piv(c)), row r times its deferred
+  // scale; padding stays zero
   if (act) {
 #pragma unroll
     for (int m = 0; m < NM; ++m) {
       const Tile& t = m == 0 ? t0 : t1;
       cf* D = m == 0 ? D0 : D1;
       int qr[3], pc[4];
+      cf sc[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) qr[i] = r0 + i < b ? (int)W.qinv[m][r0 + i] : r0 + i;
+      for (int i = 0; i < 3; ++i) {
+        qr[i] = r0 + i < b ? (int)W.qinv[m][r0 + i] : r0 + i;
+        sc[i] = r0 + i < b ? W.vs[m][r0 + i] : mk(0.0f, 0.0f);
+      }
 #pragma unroll
       for (int j = 0; j < 4; ++j) pc[j] = pcol(c0 + j < b ? (int)W.piv[m][c0 + j] : c0 + j);
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-          D[qr[i] * LD + pc[j]] = (r0 + i < b && c0 + j < b) ? t.v[i][j] : mk(0.0f, 0.0f);
+          D[qr[i] * LD + pc[j]] = (r0 + i < b && c0 + j < b) ? t.v[i][j] * sc[i] : mk(0.0f, 0.0f);
     }
   }
 }
