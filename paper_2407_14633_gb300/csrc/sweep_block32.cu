@@ -64,9 +64,11 @@ __device__ __forceinline__ void bar() {
 // banks than the 1st to 4th in a 128-bit access.
 __device__ __forceinline__ int pcol(int c) { return c + ((c >> 4) << 1); }
 
-// 1 / a through the hardware reciprocal of |a|^2 (correctly rounded), for the pivots
+// 1 / a through the approximate hardware reciprocal of |a|^2 (PTX rcp.approx.f32: at most
+// one ulp from 1 / |a|^2), for the pivots
 __device__ __forceinline__ cf crecip32(cf a) {
-  const float s = __frcp_rn(fmaf(a.re, a.re, a.im * a.im));
+  float s;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(s) : "f"(fmaf(a.re, a.re, a.im * a.im)));
   return mk(a.re * s, -a.im * s);
 }
 
@@ -822,15 +824,27 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
         bar<NW>();
         if (tid < 32)
           for (int r = tid; r < b; r += 32) {
-            float as = 0.0f, ad = 0.0f;
-            for (int j = 0; j < mS; ++j) {
-              const cf x = bT[r * LD + pcol(j)];
-              as = fmaf(x.im, x.im, fmaf(x.re, x.re, as));
+            // even and odd columns in two chains each, added at the end
+            float as0 = 0.0f, as1 = 0.0f, ad0 = 0.0f, ad1 = 0.0f;
+            const cf* tr = bT + r * LD;
+            const cf* kr = bK + r * LD;
+            for (int j = 0; j < mS; j += 2) {
+              const cf x = tr[pcol(j)];
+              as0 = fmaf(x.im, x.im, fmaf(x.re, x.re, as0));
+              if (j + 1 < mS) {
+                const cf y = tr[pcol(j + 1)];
+                as1 = fmaf(y.im, y.im, fmaf(y.re, y.re, as1));
+              }
             }
-            for (int j = 0; j < mD; ++j) {
-              const cf x = bK[r * LD + pcol(j)];
-              ad = fmaf(x.im, x.im, fmaf(x.re, x.re, ad));
+            for (int j = 0; j < mD; j += 2) {
+              const cf x = kr[pcol(j)];
+              ad0 = fmaf(x.im, x.im, fmaf(x.re, x.re, ad0));
+              if (j + 1 < mD) {
+                const cf y = kr[pcol(j + 1)];
+                ad1 = fmaf(y.im, y.im, fmaf(y.re, y.re, ad1));
+              }
             }
+            const float as = as0 + as1, ad = ad0 + ad1;
             if (r < spr)
               vr0 = fma(wS, (double)as, fma(wD, (double)ad, vr0));
             else
