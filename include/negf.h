@@ -67,7 +67,7 @@ typedef struct negf_ctx negf_ctx;
  * or NULL for a library-owned stream.  hbm_budget_bytes: cap on the library's device
  * memory (0 = no cap); allocations beyond it fail with NEGF_ENOMEM.  precision: one of
  * NEGF_PREC_*.  flag_threshold: mixed precision, the per-energy sum-rule residual (see
- * negf_out.resid) above which an energy is recomputed in FP64 (0 = default 1e-4).
+ * negf_out.resid) above which an energy is recomputed in FP64 (0 = default 1e-3).
  * edge_window: mixed precision, energies closer than this (eV) to a lead subband edge are
  * recomputed in FP64 (0 = default 0.002).  fault_alloc_after:
  * host-side fault injection for tests, the n-th arena allocation fails (0 = off).

@@ -452,7 +452,7 @@ int negf_create(negf_ctx** out, const negf_opts* opts) {
     delete c;
     return NEGF_EINVAL;
   }
-  if (c->opts.flag_threshold <= 0.0) c->opts.flag_threshold = 1e-4;
+  if (c->opts.flag_threshold <= 0.0) c->opts.flag_threshold = 1e-3;
   if (c->opts.edge_window <= 0.0) c->opts.edge_window = 0.002;
   c->ordinal = c->opts.device_ordinal;
   int ndev = 0;

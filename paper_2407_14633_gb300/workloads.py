@@ -111,7 +111,7 @@ def mixed_precision(tubes=(17, 26, 34), N=1024, n_energies=4096,
     of 0 switches that criterion off) vs the plain complex64 sweep; errors per output against
     the complex128 result, and which criterion flagged how many energies."""
     out = {}
-    thr, gthr = 1e-4, 20.0
+    thr, gthr = 1e-3, 20.0
     for n_tube in tubes:
         w = synth.mixed_precision(n_tube=n_tube, N=N, n_energies=n_energies)
         E = w["E"]
