@@ -597,7 +597,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
   // end of a short group would trail the launch (measured: with 3.4 lanes per CTA the fused
   // kernel took 1.25x the two passes).  The launch shape then follows the size policy.
   constexpr int FUSE_LANES_PER_CTA = 16;
-  if (P.prec == NEGF_PREC_MIXED && !c->opts.mixed_two_pass)
+  if (P.prec == NEGF_PREC_MIXED && c->opts.mixed_two_pass <= 0)
     for (int g = 5; g < NGROUPS; ++g) {
       if (group_class(g) != 2 || !P.ncls[g]) continue;
       const int w = blk_eff_width(true, P.gb[g], P.gm[g], P.gw[g]);

@@ -76,3 +76,16 @@ def test_mixed_workload_against_oracle(name, bounds):
     e = errors(r)
     print(name, e)
     assert all(e[k] < bounds[k] for k in bounds), (e, bounds)
+
+
+
+def test_in_kernel_re_sweep_is_bitwise_the_second_pass():
+    """At full size (4096 lanes, several per resident CTA) the complex64 kernel re-sweeping its
+    flagged lanes in FP64 itself gives bitwise the outputs and flags of the second pass."""
+    from paper_2407_14633_gb300 import negf
+    a = run(negf.PREC_MIXED, mixed_two_pass=-1)
+    b = run(negf.PREC_MIXED, mixed_two_pass=1)
+    assert np.array_equal(a["flags"], b["flags"]) and a["flags"].sum() > 0
+    for k in ("n", "T", "n_cont", "n_real"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["I"] == b["I"]
