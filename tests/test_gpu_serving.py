@@ -47,6 +47,37 @@ def test_served_equals_single_solve_loop():
     assert np.array_equal(r["n"], s["n"]) and np.array_equal(r["U"], s["U"])
 
 
+def test_served_requests_match_oracle():
+    """Two requests served together by continuous batching, each against the oracle's own loop
+    (Alg. 3 with the 1D Poisson stand-in, Eq. GR leads, Alg. 1 / Alg. 2 as read) on the same
+    inputs: the same iteration count, n and U within 1e-9, the current within 1e-9."""
+    from paper_2407_14633_gb300 import negf
+    from oracle import charge as ochg
+    from oracle import model as omdl
+    from oracle import quadrature as oq
+    from oracle import selfconsistent as osc
+    from tests.cases import rel_inf
+    reqs = [(24, (6,), 0.2, 0.1), (30, (6, 5), 0.1, -0.1)]
+    n_real, n_cont, E_B, tol = 48, 16, -10.0, 1e-9
+    U0s = [np.linspace(0.0, -vds, n) + 0.02 * np.sin(np.arange(n)) for n, _, vds, _ in reqs]
+    with negf.Context() as ctx:
+        tks = [ctx.submit(n, list(m), vds, vgs, n_real=n_real, n_cont=n_cont, E_B=E_B, tol=tol, U0=U0)
+               for (n, m, vds, vgs), U0 in zip(reqs, U0s)]
+        while any(ctx.poll(t) is None for t in tks):
+            ctx.serve_step()
+        res = [ctx.poll(t) for t in tks]
+    for (n, m, vds, vgs), U0, r in zip(reqs, U0s, res):
+        dev = omdl.cnt_build("mode", 17, -2.7, n, 0.0, -vds, modes=m)
+        grid = oq.bias_grid(0.0, -vds, 0.025, n_real, n_cont, E_B, 1e-6)
+        n0 = ochg.neutral_charge(dev, n_cont, E_B)
+        pp = osc.PoissonParams(kappa=osc.kappa_from_geometry(), U_G=-vgs, U_S=0.0, U_D=-vds)
+        o = osc.sc_solve(lambda U: ochg.negf_evaluate(dev, U, grid), U0, n0, pp, zeta=0.1, M=64, tol=tol)
+        assert r["converged"] and o["converged"]
+        assert r["iterations"] == o["iterations"]
+        assert rel_inf(r["n"], o["n"]) < 1e-9 and rel_inf(r["U"], o["U"]) < 1e-9
+        assert abs(r["I"] - o["I"]) <= 1e-9 * max(abs(o["I"]), 1e-15)
+
+
 def test_budget_admission_limits_active_slots():
     from paper_2407_14633_gb300 import negf
     # ~7 MB of per-request buffers and ~31 MB of sweep staging per resident block at N = 3000:
