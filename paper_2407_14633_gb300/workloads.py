@@ -170,9 +170,10 @@ def mixed_precision(tubes=(17, 26, 34), N=1024, n_energies=4096,
 def serving_sweep(n_requests=256, rate_factor=2.0, tol=1e-5, M=64):
     """Self-consistent I-V requests (the first n_requests of the seeded 256-request stream): a
     sequential loop of negf_sc_solve calls, then the continuous-batching server with Poisson
-    arrivals at rate_factor x the sequential rate, then the server with every request queued
-    at once (its capacity).  tol is the convergence threshold of Alg. 3 (1e-5).  Rates are
-    given over all requests and over the converged ones alone."""
+    arrivals at rate_factor x the sequential rate, the sequential loop again under the same
+    arrivals, and the server with every request queued at once (its capacity).  tol is the
+    convergence threshold of Alg. 3 (1e-5).  Rates are given over all requests and over the
+    converged ones alone; latencies run from a request's arrival to its result."""
     w = synth.serving_sweep(n_requests=256)
     w["requests"] = w["requests"][:n_requests]
     w["unit_gaps"] = w["unit_gaps"][:n_requests]
@@ -224,12 +225,23 @@ def serving_sweep(n_requests=256, rate_factor=2.0, tol=1e-5, M=64):
             ts, tst, td = ctx.request_times(tk)
             lat.append(td - ts)
             served.append(ctx.poll(tk))
-    # the sequential loop under the same arrivals: one solve at a time in arrival order, each
-    # taking its measured time (a single-server queue)
-    fin, seq_q = 0.0, []
-    for arr, dt in zip(arrivals, seq_lat):
-        fin = max(fin, arr) + dt
-        seq_q.append(fin - arr)
+    # the sequential loop under the same arrivals, run: each request is solved once it has
+    # arrived and the one before it is done; its latency runs from its arrival
+    seq_q = []
+    with negf.Context() as ctx:
+        t0 = time.perf_counter()
+        for arr, q in zip(arrivals, reqs):
+            idle = arr - (time.perf_counter() - t0)
+            if idle > 0:
+                time.sleep(idle)
+            dev = ctx.device_create(q["N"], n_chains=len(q["modes"]))
+            ctx.build_cnt_modespace(dev, w["n_tube"], w["t"], list(q["modes"]), 0.0, -q["V_DS"])
+            E_B = -q["V_DS"] - 3.0 * abs(w["t"]) - 1.0
+            ctx.set_grid_spec(dev, 0.0, -q["V_DS"], w["kT"], w["eta"], E_B, q["n_real"], q["n_cont"])
+            ctx.sc_solve(dev, q["V_DS"], q["V_GS"], np.linspace(0.0, -q["V_DS"], q["N"]), kappa, M=M, tol=tol,
+                         check=False)
+            ctx.device_destroy(dev)
+            seq_q.append(time.perf_counter() - t0 - arr)
     # capacity: all requests queued at t = 0
     with negf.Context() as ctx:
         t0 = time.perf_counter()
