@@ -321,12 +321,12 @@ __device__ __forceinline__ void talpha(Tile& t, int l, int L, int b, int rpb, in
 }
 
 // Scratch of the inverses: per matrix and step parity the pivot column and the pivot row,
-// the pivot order and each row's deferred scale (1 / its pivot).
+// and the pivot order.  (Each row's deferred scale, 1 / its pivot, goes to a matrix buffer that
+// is free while the inverse runs.)
 template <int NW>
 struct InvBuf {
   cf colb[2][2][T32<NW>::PR];
   cf rowb[2][2][T32<NW>::LD];
-  cf vs[2][T32<NW>::BMAX];
   unsigned char piv[2][64];
   unsigned char qinv[2][64];
 };
@@ -391,10 +391,12 @@ __device__ __forceinline__ int gj_pivot(const cf* colb, int b, unsigned long lon
 // the pivot of row i, q the step of row i; D0, D1 receive the inverses, rows rescaled, in
 // place of their rows and columns (zeros outside b x b).  Pivot
 // columns and rows alternate between two buffers, so a step's writes never meet a slower
-// warp's reads of the step before.  The caller synchronises before reading D0, D1.
+// warp's reads of the step before.  vs (2 BMAX elements) is scratch for the rows' scales; it
+// must not be read by any thread between the call and the next full store into it.  The caller
+// synchronises before reading D0, D1.
 template <int NW, int NM>
-__device__ __forceinline__ void tinv(Tile& t0, Tile& t1, cf* D0, cf* D1, int b, InvBuf<NW>& W, int tid, bool act,
-                                     int tc, int r0, int c0) {
+__device__ __forceinline__ void tinv(Tile& t0, Tile& t1, cf* D0, cf* D1, int b, InvBuf<NW>& W, cf* vs, int tid,
+                                     bool act, int tc, int r0, int c0) {
   using C = T32<NW>;
   constexpr int LD = C::LD;
   const int lane = tid & 31;
@@ -437,11 +439,11 @@ __device__ __forceinline__ void tinv(Tile& t0, Tile& t1, cf* D0, cf* D1, int b, 
         if (tid == 0) {
           W.piv[0][k] = (unsigned char)p0;
           W.qinv[0][p0] = (unsigned char)k;
-          W.vs[0][p0] = ip0;
+          vs[p0] = ip0;
           if (NM > 1) {
             W.piv[1][k] = (unsigned char)p1;
             W.qinv[1][p1] = (unsigned char)k;
-            W.vs[1][p1] = ip1;
+            vs[T32<NW>::BMAX + p1] = ip1;
           }
         }
         bar<NW>();
@@ -465,7 +467,7 @@ __device__ __forceinline__ void tinv(Tile& t0, Tile& t1, cf* D0, cf* D1, int b, 
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         qr[i] = r0 + i < b ? (int)W.qinv[m][r0 + i] : r0 + i;
-        sc[i] = r0 + i < b ? W.vs[m][r0 + i] : mk(0.0f, 0.0f);
+        sc[i] = r0 + i < b ? vs[m * T32<NW>::BMAX + r0 + i] : mk(0.0f, 0.0f);
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) pc[j] = pcol(c0 + j < b ? (int)W.piv[m][c0 + j] : c0 + j);
@@ -501,7 +503,6 @@ template <int NW>
 struct Smem32 {
   cf mat[T32<NW>::NBUF][T32<NW>::MAT];
   InvBuf<NW> inv;
-  cd sigS[T32<NW>::BMAX], sigD[T32<NW>::BMAX];   // lead rings have m <= b sites
   double sqS[T32<NW>::BMAX], sqD[T32<NW>::BMAX];
   int sinvS[T32<NW>::BMAX], sinvD[T32<NW>::BMAX];
   double red[B32_RED];
@@ -513,7 +514,7 @@ struct Smem32 {
 // FUSE: re-sweep flagged real-axis lanes in FP64 in the same CTA (mixed precision; the FP64
 // compact layout of the block sweep in this CTA's shared memory)
 template <int NW, bool FUSE>
-__global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) sweep_blk32_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 3)) sweep_blk32_kernel(SweepArgs a) {
   using Cf = T32<NW>;
   constexpr int LD = Cf::LD, NT = Cf::NT, NTA = Cf::NTA, MAT = Cf::MAT;
   extern __shared__ __align__(16) unsigned char sm_b32[];
@@ -596,12 +597,16 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
       S.sinvD[r] = -1;
     }
     __syncthreads();
+    // the circulant leads' Sigma rows (FP64) sit in the staging slot of y_0, which the sweep
+    // never stages (y_0 = 0): they are read at the first and last layer only
+    cd* const sigS = reinterpret_cast<cd*>(yl_of(0));
+    cd* const sigD = sigS + T32<NW>::BMAX;
     for (int s = tid; s < mS; s += NT) S.sinvS[LS.sites[s]] = s;
     for (int s = tid; s < mD; s += NT) S.sinvD[LDv.sites[s]] = s;
     for (int side = 0; side < 2; ++side) {
       const LeadView& Lv = C.lead[side];
       if (Lv.gen) continue;
-      cd* row = side ? S.sigD : S.sigS;
+      cd* row = side ? sigD : sigS;
       double* sq = side ? S.sqD : S.sqS;
       const int m = Lv.m;
       for (int j = tid; j < m; j += NT) {
@@ -672,7 +677,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
           tzero(ta);
           tcol<LD, false>(ta, bT, ccnt, cidx, cval, kmax, b, r0, c0);   // y_l = X H_{l-1,l}
           gstore<NTA>(yl_of(l), tid, ta);
-          talpha(ta, l, L, b, rpb, spr, eps, S.ip, S.sigS, S.sigD, S.sinvS, S.sinvD, r0, c0);
+          talpha(ta, l, L, b, rpb, spr, eps, S.ip, sigS, sigD, S.sinvS, S.sinvD, r0, c0);
           if (real) tgemm<LD>(tr_, bT, bR, b, r0, c0);                   // R_l = X R_{l-1}
         }
         if (real) {
@@ -685,7 +690,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
       } else {
         if (act) {
           tzero(ta);
-          talpha(ta, 0, L, b, rpb, spr, eps, S.ip, S.sigS, S.sigD, S.sinvS, S.sinvD, r0, c0);
+          talpha(ta, 0, L, b, rpb, spr, eps, S.ip, sigS, sigD, S.sinvS, S.sinvD, r0, c0);
           if (real) {
 #pragma unroll
             for (int i = 0; i < 3; ++i)
@@ -695,7 +700,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
           }
         }
       }
-      tinv<NW, 1>(ta, ta, bG, nullptr, b, S.inv, tid, act, tc, r0, c0);   // gL_l = (alpha_l - y_l)^{-1}
+      tinv<NW, 1>(ta, ta, bG, nullptr, b, S.inv, bT, tid, act, tc, r0, c0);   // gL_l = (alpha_l - y_l)^{-1}
       bar<NW>();
       if (act) {   // stage gL_l (logical tile, real-axis lanes) and track its largest entry
         Tile tg;
@@ -738,14 +743,14 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
     if (L > 1) {
       if (act) {
         tzero(ta);
-        talpha(ta, L - 1, L, b, rpb, spr, eps, S.ip, S.sigS, S.sigD, S.sinvS, S.sinvD, r0, c0);
+        talpha(ta, L - 1, L, b, rpb, spr, eps, S.ip, sigS, sigD, S.sinvS, S.sinvD, r0, c0);
         if (real) {
           Tile tg;
           gload<NTA>(tg, gl_of(L - 2), tid);
           tstore<LD>(bGL, tg, r0, c0);
         }
       }
-      tinv<NW, 1>(ta, ta, bGR, nullptr, b, S.inv, tid, act, tc, r0, c0);  // gR_{L-1} = alpha_{L-1}^{-1}
+      tinv<NW, 1>(ta, ta, bGR, nullptr, b, S.inv, bT, tid, act, tc, r0, c0);  // gR_{L-1} = alpha_{L-1}^{-1}
     }
     __syncthreads();
 
@@ -792,7 +797,7 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
           }
           tzero(tm1);
           tcol<LD, true>(tm1, bT, rcnt, ridx, rval, kmax, b, r0, c0);          // x_l = W1 H_{l+1,l}
-          talpha(tm1, l, L, b, rpb, spr, eps, S.ip, S.sigS, S.sigD, S.sinvS, S.sinvD, r0, c0);
+          talpha(tm1, l, L, b, rpb, spr, eps, S.ip, sigS, sigD, S.sinvS, S.sinvD, r0, c0);
         }
         bar<NW>();
         if (act && real) tstore<LD>(bK, tk, r0, c0);
@@ -806,9 +811,9 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 2)) swe
           }
           // G_ll = (alpha_l - x_l - y_l)^{-1} into bG (free since K_l was formed), gR_l =
           // (alpha_l - x_l)^{-1} into bGR (gR_{l+1} was last read by W1)
-          tinv<NW, 2>(ta, tm1, bG, bGR, b, S.inv, tid, act, tc, r0, c0);
+          tinv<NW, 2>(ta, tm1, bG, bGR, b, S.inv, bT, tid, act, tc, r0, c0);
         } else {
-          tinv<NW, 1>(tm1, tm1, bG, nullptr, b, S.inv, tid, act, tc, r0, c0);   // G_00 = (alpha_0 - x_0)^{-1}
+          tinv<NW, 1>(tm1, tm1, bG, nullptr, b, S.inv, bT, tid, act, tc, r0, c0);   // G_00 = (alpha_0 - x_0)^{-1}
         }
         bar<NW>();
       }
