@@ -150,3 +150,21 @@ def test_wide_tube_mixed_precision_bound(n_tube):
     assert max(errs.values()) < MIXED_DEFAULT_BOUND, errs
     # contour lanes stay FP64
     assert rel_inf(r["n_cont"], o["n_cont"]) < TOL
+
+
+@pytest.mark.parametrize("n_tube", [37, 40])
+def test_blocks_wider_than_the_register_tiles(n_tube):
+    """Ring blocks wider than 36 (past the widest register-tile class): the shared-memory
+    kernels in FP64 (the wider layout: four b x b and three b x m buffers) and in complex64, and
+    the mixed path on top of them, against the oracle on a short tube."""
+    from paper_2407_14633_gb300 import negf
+    N = 4
+    p = case_params("real", N, 24, 8, synth.sinusoid_profile(N, 3), mu_D=-0.3, n_tube=n_tube, U_S=0.0,
+                    U_D=-0.3)
+    o = run_oracle(p, chunk=8)
+    r, _ = _run(p)
+    print("(%d,0) FP64: %s" % (n_tube, _check(p, r, o)))
+    r, _ = _run(p, precision=negf.PREC_FP32)
+    print("(%d,0) complex64: %s" % (n_tube, _check(p, r, o, tol=1e-3)))
+    r, _ = _run(p, precision=negf.PREC_MIXED)
+    print("(%d,0) mixed: %s" % (n_tube, _check(p, r, o, tol=MIXED_DEFAULT_BOUND)))
