@@ -199,3 +199,26 @@ def test_general_lead_arguments_and_limits(ctx):
     with pytest.raises(negf.NegfError) as e:
         ctx.compute([dev])
     assert e.value.status == negf.ENOTCONVERGED
+
+
+@pytest.mark.parametrize("n_tube,N,m", [(7, 9, 4), (17, 6, 17)])
+def test_general_leads_in_complex64_and_mixed_precision(n_tube, N, m):
+    """General leads in the complex64 sweeps (the per-energy Sigma blocks and Gamma factors of
+    the decimation, rounded once to complex64 in the sweep): the plain complex64 sweep within
+    1e-3 of the oracle, the mixed path within its stated bound (n 5e-5, T 1e-4, I 2e-5)."""
+    from paper_2407_14633_gb300 import negf
+    mu_S, mu_D, n_real, n_cont = 0.0, -0.3, 40, 12
+    U = synth.sinusoid_profile(N, 9, amplitude=0.2)
+    sites = list(range(m)) if m == n_tube else [0, 2, 3, 6][:m]
+    leads = [synth.general_lead(m, 100 + n_tube), synth.general_lead(m, 200 + n_tube)]
+    od = oracle_tube(n_tube, N, 0.05, -0.3, leads, sites)
+    o = ochg.negf_evaluate(od, U, oq.bias_grid(mu_S, mu_D, KT, n_real, n_cont, E_B, ETA), method="sancho")
+    for prec, bound in ((negf.PREC_FP32, (1e-3, 1e-3, 1e-3)), (negf.PREC_MIXED, (5e-5, 1e-4, 2e-5))):
+        with negf.Context(precision=prec) as c2:
+            dev = lib_tube(c2, n_tube, N, U, 0.05, -0.3, leads, sites)
+            c2.set_grid_spec(dev, mu_S, mu_D, KT, ETA, E_B, n_real, n_cont)
+            r = c2.compute([dev])[0]
+        errs = (rel_inf(r["n"], o["n"]), rel_inf(r["T"], o["T"]),
+                current_err(r["I"], o["I"], 2.0, mu_S - mu_D))
+        print("(%d,0) m = %d precision %d: n %.2e T %.2e I %.2e" % ((n_tube, m, prec) + errs))
+        assert all(e < b for e, b in zip(errs, bound)), (errs, bound)
