@@ -30,16 +30,48 @@ __device__ __forceinline__ int next_item(int* counter, int lane) {
   return __shfl_sync(0xffffffffu, it, 0);
 }
 
-// flush ring slots [base, base + count) of the 32 x 33 transpose buffer into `dst`
-__device__ __forceinline__ void flush_rings(double* red, int lane, int count, double* dst) {
+// flush ring slots [base, base + count) of the 32 x 33 transpose buffer into `dst`; the
+// buffer holds the sweep's element type (the complex64 sweep accumulates its per-lane ring
+// contributions in FP32: the FP64 pipe of this part is 1/62 of the FP32 one)
+template <typename T>
+__device__ __forceinline__ void flush_rings(T* red, int lane, int count, double* dst) {
   __syncwarp();
   if (lane < count) {
-    double s = 0.0;
+    T s = T(0);
 #pragma unroll 8
     for (int j = 0; j < 32; ++j) s += red[lane * 33 + j];
-    dst[lane] = s;
+    dst[lane] = (double)s;
   }
   __syncwarp();
+}
+
+// 1 / x: IEEE division in FP64; in FP32 the hardware's approximate reciprocal (PTX
+// rcp.approx.f32, at most one ulp from the correctly rounded value)
+template <typename T>
+__device__ __forceinline__ T recip(T x);
+template <>
+__device__ __forceinline__ double recip<double>(double x) {
+  return 1.0 / x;
+}
+template <>
+__device__ __forceinline__ float recip<float>(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// eps - U on the diagonal of a 2 x 2 layer: in FP64; in the complex64 sweep from the operands
+// rounded to FP32 (within an ulp of the larger of |eps| and |U|; the 1 x 1 sweep reads it
+// formed in FP64 and rounded once by prep_kernel)
+template <typename T>
+__device__ __forceinline__ T eps_minus(double e, double u);
+template <>
+__device__ __forceinline__ double eps_minus<double>(double e, double u) {
+  return e - u;
+}
+template <>
+__device__ __forceinline__ float eps_minus<float>(double e, double u) {
+  return (float)e - (float)u;
 }
 
 template <typename T>
@@ -70,7 +102,7 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-  double* red = sm_b1 + wib * (32 * 33);
+  T* red = reinterpret_cast<T*>(sm_b1) + wib * (32 * 33);
   T* st = reinterpret_cast<T*>(a.stage + (long long)gw * a.stage_stride);
 
   for (;;) {
@@ -138,7 +170,7 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
         if (W.kind == 0) ql = p * ql;
         if (want_r) qu = p * qu;
       }
-      const T r = T(1) / fma(x.re, x.re, x.im * x.im);
+      const T r = recip<T>(fma(x.re, x.re, x.im * x.im));
       gl = mk(x.re * r, -x.im * r);
       rl = r;
       if (a.growth) rmaxg = r > rmaxg ? r : rmaxg;
@@ -156,8 +188,9 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
     cx<T> G = gl;             // G_{L-1,L-1}
     T c = abs2(G);            // |G_{l,L-1}|^2
     // sum-rule residual of the lane: max(0, max_l (A_S + A_D + 2 Im G)_ll) / max_l |2 Im G_ll|
-    double rnum = 0.0, rden = 0.0;
-    const double wDg = wD * gamD;
+    // (in the element type, as the per-layer contributions)
+    T rnum = T(0), rden = T(0);
+    const T wDg = (T)(wD * gamD);
     T pn = T(0);              // |h_{l,l+1}|^2 |gL_l|^2, read one layer ahead
     for (int l = L - 1; l >= 0; --l) {
       const T* s = st + (long long)l * nf * 32;
@@ -169,21 +202,21 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
         if (W.kind == 0) c = pn * c;         // |G_{l,L-1}|^2
       }
       if (W.kind == 0) pn = s[64 + lane];
-      double v;
+      T v;
       if (W.kind == 0) {
         const T q = s[96 + lane];
-        v = fma(wDg, (double)c, (double)(q * abs2(G)));
+        v = fma(wDg, c, q * abs2(G));
         if (want_r) {
           // A_S + A_D + 2 Im G <= 0 up to rounding (equality up to 2 eta |G|^2 terms)
-          const double as = gamS * (double)s[128 + lane] * (double)abs2(G);
-          const double gim = (double)G.im;
-          rnum = fmax(rnum, as + gamD * (double)c + 2.0 * gim);
-          rden = fmax(rden, fabs(2.0 * gim));
+          const T as = (T)gamS * s[128 + lane] * abs2(G);
+          const T gim = G.im;
+          rnum = fmax(rnum, as + (T)gamD * c + T(2) * gim);
+          rden = fmax(rden, fabs(T(2) * gim));
         }
       } else {
-        v = kap.re * (double)G.im + kap.im * (double)G.re;
+        v = (T)kap.re * G.im + (T)kap.im * G.re;
       }
-      if (a.ring_cap && l == a.cap_ring && W.kind == 0 && act) a.ring_cap[W.tout + lane] = v;
+      if (a.ring_cap && l == a.cap_ring && W.kind == 0 && act) a.ring_cap[W.tout + lane] = (double)v;
       red[(l & 31) * 33 + lane] = v;
       if ((l & 31) == 0) {
         const int cnt = min(32, L - l);
@@ -192,7 +225,7 @@ __global__ void __launch_bounds__(256) sweep_b1_kernel(SweepArgs a) {
     }
     if (W.kind == 0 && act) {
       a.Tpart[W.tout + lane] = gamS * gamD * (double)c;
-      if (want_r) a.resid[W.tout + lane] = rnum / fmax(rden, 1e-300);
+      if (want_r) a.resid[W.tout + lane] = (double)rnum / fmax((double)rden, 1e-300);
       if (a.growth) a.growth[W.tout + lane] = sqrt((double)rmaxg);
     }
   }
@@ -217,7 +250,8 @@ __device__ __forceinline__ m2<T> mul2(const m2<T>& A, const m2<T>& B) {
 template <typename T>
 __device__ __forceinline__ m2<T> inv2(const m2<T>& A) {
   cx<T> det = A.a[0][0] * A.a[1][1] - A.a[0][1] * A.a[1][0];
-  cx<T> id = crecip(det);
+  const T s = recip<T>(fma(det.re, det.re, det.im * det.im));
+  const cx<T> id = mk(det.re * s, -det.im * s);
   m2<T> B;
   B.a[0][0] = A.a[1][1] * id;
   B.a[1][1] = A.a[0][0] * id;
@@ -244,7 +278,7 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-  double* red = sm_b2 + wib * (32 * 33);
+  T* red = reinterpret_cast<T*>(sm_b2) + wib * (32 * 33);
   T* st = reinterpret_cast<T*>(a.stage + (long long)gw * a.stage_stride);
   constexpr int NF = 12;  // gL (8 reals) + R (4 reals)
 
@@ -293,8 +327,8 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
         for (int j = 0; j < 2; ++j) A.a[i][j] = mk(T(0), T(0)) - A.a[i][j];
       // ring of site a: 2l + a for unit cells (rpb = 2), l for a two-site ring (rpb = 1)
       const int ring0 = l * rpb, ring1 = l * rpb + (rpb - 1);
-      A.a[0][0] = A.a[0][0] + mk((T)(eps.re - U[ring0]), (T)eps.im);
-      A.a[1][1] = A.a[1][1] + mk((T)(eps.re - U[ring1]), (T)eps.im);
+      A.a[0][0] = A.a[0][0] + mk(eps_minus<T>(eps.re, U[ring0]), (T)eps.im);
+      A.a[1][1] = A.a[1][1] + mk(eps_minus<T>(eps.re, U[ring1]), (T)eps.im);
       if (l == 0) A.a[siteS][siteS] = A.a[siteS][siteS] - mk((T)sS.re, (T)sS.im);
       if (l == L - 1) A.a[siteD][siteD] = A.a[siteD][siteD] - mk((T)sD.re, (T)sD.im);
       cx<T> Rn[2];
@@ -341,7 +375,7 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
 
     // backward: G_ll, K_l = G_{l,L-1} L_D, P_l = G_ll R_l
     const bool want_r = a.resid != nullptr && W.kind == 0;
-    double rnum = 0.0, rden = 0.0;   // sum-rule residual, as in the 1 x 1 sweep
+    T rnum = T(0), rden = T(0);   // sum-rule residual, as in the 1 x 1 sweep
     m2<T> G = gl;
     cx<T> K[2];
     K[0] = scale(G.a[0][siteD], lD);
@@ -372,29 +406,29 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
           K[1] = Kn[1];
         }
       }
-      double v0, v1;
+      T v0, v1;   // in the element type, as the 1 x 1 sweep
       if (W.kind == 0) {
         cx<T> Rl[2];
         Rl[0] = mk(s[8 * 32 + lane], s[9 * 32 + lane]);
         Rl[1] = mk(s[10 * 32 + lane], s[11 * 32 + lane]);
         cx<T> P0 = cmac(G.a[0][0] * Rl[0], G.a[0][1], Rl[1]);
         cx<T> P1 = cmac(G.a[1][0] * Rl[0], G.a[1][1], Rl[1]);
-        v0 = wS * (double)abs2(P0) + wD * (double)abs2(K[0]);
-        v1 = wS * (double)abs2(P1) + wD * (double)abs2(K[1]);
+        v0 = (T)wS * abs2(P0) + (T)wD * abs2(K[0]);
+        v1 = (T)wS * abs2(P1) + (T)wD * abs2(K[1]);
         if (want_r) {
-          const double g0 = (double)G.a[0][0].im, g1 = (double)G.a[1][1].im;
-          rnum = fmax(rnum, (double)abs2(P0) + (double)abs2(K[0]) + 2.0 * g0);
-          rnum = fmax(rnum, (double)abs2(P1) + (double)abs2(K[1]) + 2.0 * g1);
-          rden = fmax(rden, fmax(fabs(2.0 * g0), fabs(2.0 * g1)));
+          const T g0 = G.a[0][0].im, g1 = G.a[1][1].im;
+          rnum = fmax(rnum, abs2(P0) + abs2(K[0]) + T(2) * g0);
+          rnum = fmax(rnum, abs2(P1) + abs2(K[1]) + T(2) * g1);
+          rden = fmax(rden, fmax(fabs(T(2) * g0), fabs(T(2) * g1)));
         }
       } else {
-        v0 = kap.re * (double)G.a[0][0].im + kap.im * (double)G.a[0][0].re;
-        v1 = kap.re * (double)G.a[1][1].im + kap.im * (double)G.a[1][1].re;
+        v0 = (T)kap.re * G.a[0][0].im + (T)kap.im * G.a[0][0].re;
+        v1 = (T)kap.re * G.a[1][1].im + (T)kap.im * G.a[1][1].re;
       }
       // rings of the layer -> transpose slots ring & 31
       const int r0 = l * rpb;
       if (a.ring_cap && W.kind == 0 && act && a.cap_ring >= r0 && a.cap_ring < r0 + rpb)
-        a.ring_cap[W.tout + lane] = rpb == 2 ? (a.cap_ring == r0 ? v0 : v1) : v0 + v1;
+        a.ring_cap[W.tout + lane] = (double)(rpb == 2 ? (a.cap_ring == r0 ? v0 : v1) : v0 + v1);
       if (rpb == 2) {
         red[(r0 & 31) * 33 + lane] = v0;
         red[((r0 + 1) & 31) * 33 + lane] = v1;
@@ -409,7 +443,7 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
     if (W.kind == 0 && act) {
       // T = Tr[Gamma_S G_{0,L-1} Gamma_D G_{0,L-1}^dag] = Gamma_S |K_0[siteS]|^2
       a.Tpart[W.tout + lane] = gamS * (double)abs2(K[siteS]);
-      if (want_r) a.resid[W.tout + lane] = rnum / fmax(rden, 1e-300);
+      if (want_r) a.resid[W.tout + lane] = (double)rnum / fmax((double)rden, 1e-300);
       if (a.growth) a.growth[W.tout + lane] = sqrt((double)gmax2);
     }
   }
