@@ -480,6 +480,12 @@ __device__ __forceinline__ void tinv(Tile& t0, Tile& t1, cf* D0, cf* D1, int b, 
   }
 }
 
+__device__ __forceinline__ float wsumf(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
 __device__ __forceinline__ double wsumd(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -570,6 +576,8 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 3)) swe
       eps = D.z[k];
       kap = scale(D.c[k], g / 3.14159265358979323846);
     }
+    const float wSf = (float)wS, wDf = (float)wD;
+    const cf kapf = mk((float)kap.re, (float)kap.im);
 
     if (tid == 0) {
       ItemPtrs q;
@@ -819,7 +827,8 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 3)) swe
       }
       // per-site contributions of layer l, summed per ring: rows on warp 0 with a fixed lane
       // mapping and fixed-order row sums, so the result does not depend on the CTA width
-      double vr0 = 0.0, vr1 = 0.0;   // the layer's first and second ring (rpb <= 2)
+      // (in FP32: an FP64 operation costs the FP64 pipe about as much as 60 FP32 ones)
+      float vr0 = 0.0f, vr1 = 0.0f;   // the layer's first and second ring (rpb <= 2)
       if (real) {
         if (act) {
           Tile tp;
@@ -851,9 +860,9 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 3)) swe
             }
             const float as = as0 + as1, ad = ad0 + ad1;
             if (r < spr)
-              vr0 = fma(wS, (double)as, fma(wD, (double)ad, vr0));
+              vr0 = fmaf(wSf, as, fmaf(wDf, ad, vr0));
             else
-              vr1 = fma(wS, (double)as, fma(wD, (double)ad, vr1));
+              vr1 = fmaf(wSf, as, fmaf(wDf, ad, vr1));
             if (a.resid) {
               rnum = fmaxf(rnum, fmaf(2.0f, bG[r * LD + pcol(r)].im, as + ad));
               rden = fmaxf(rden, fabsf(2.0f * bG[r * LD + pcol(r)].im));
@@ -863,15 +872,15 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 3)) swe
         for (int r = tid; r < b; r += 32) {
           const cf gd = bG[r * LD + pcol(r)];
           if (r < spr)
-            vr0 = fma(kap.re, (double)gd.im, fma(kap.im, (double)gd.re, vr0));
+            vr0 = fmaf(kapf.re, gd.im, fmaf(kapf.im, gd.re, vr0));
           else
-            vr1 = fma(kap.re, (double)gd.im, fma(kap.im, (double)gd.re, vr1));
+            vr1 = fmaf(kapf.re, gd.im, fmaf(kapf.im, gd.re, vr1));
         }
       }
       if (tid < 32)
         for (int q = 0; q < rpb; ++q) {
-          const double s = wsumd(q == 0 ? vr0 : vr1);
-          if (tid == 0) part[l * rpb + q] = s;
+          const float s = wsumf(q == 0 ? vr0 : vr1);
+          if (tid == 0) part[l * rpb + q] = (double)s;
         }
       bar<NW>();
     }
