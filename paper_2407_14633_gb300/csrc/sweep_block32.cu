@@ -276,6 +276,8 @@ struct ItemPtrs {
   int kmax, mS, mD;
   int hd_step, cp_step;   // layer steps of hd and of the sparse forms (0: every layer the same)
   int pad;
+  float wS, wD;           // the lane's weights of A_S and A_D in the ring sums (real axis)
+  cf kap;                 // and of G (contour)
 };
 
 // In place: t := alpha_l - t on r, c < b (0 elsewhere), alpha_l = eps I - H_ll - U_ring -
@@ -576,8 +578,6 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 3)) swe
       eps = D.z[k];
       kap = scale(D.c[k], g / 3.14159265358979323846);
     }
-    const float wSf = (float)wS, wDf = (float)wD;
-    const cf kapf = mk((float)kap.re, (float)kap.im);
 
     if (tid == 0) {
       ItemPtrs q;
@@ -597,6 +597,9 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 3)) swe
       q.hd_step = C.hd_step;
       q.cp_step = C.cp_step;
       q.pad = 0;
+      q.wS = (float)wS;
+      q.wD = (float)wD;
+      q.kap = mk((float)kap.re, (float)kap.im);
       S.ip = q;
     }
     // ---- lead self-energies in FP64 (per-mode roots, circulant first rows), site maps
@@ -860,9 +863,9 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 3)) swe
             }
             const float as = as0 + as1, ad = ad0 + ad1;
             if (r < spr)
-              vr0 = fmaf(wSf, as, fmaf(wDf, ad, vr0));
+              vr0 = fmaf(S.ip.wS, as, fmaf(S.ip.wD, ad, vr0));
             else
-              vr1 = fmaf(wSf, as, fmaf(wDf, ad, vr1));
+              vr1 = fmaf(S.ip.wS, as, fmaf(S.ip.wD, ad, vr1));
             if (a.resid) {
               rnum = fmaxf(rnum, fmaf(2.0f, bG[r * LD + pcol(r)].im, as + ad));
               rden = fmaxf(rden, fabsf(2.0f * bG[r * LD + pcol(r)].im));
@@ -872,9 +875,9 @@ __global__ void __launch_bounds__(32 * NW, NW == 1 ? 10 : (NW == 2 ? 4 : 3)) swe
         for (int r = tid; r < b; r += 32) {
           const cf gd = bG[r * LD + pcol(r)];
           if (r < spr)
-            vr0 = fmaf(kapf.re, gd.im, fmaf(kapf.im, gd.re, vr0));
+            vr0 = fmaf(S.ip.kap.re, gd.im, fmaf(S.ip.kap.im, gd.re, vr0));
           else
-            vr1 = fmaf(kapf.re, gd.im, fmaf(kapf.im, gd.re, vr1));
+            vr1 = fmaf(S.ip.kap.re, gd.im, fmaf(S.ip.kap.im, gd.re, vr1));
         }
       }
       if (tid < 32)
