@@ -18,9 +18,13 @@
 //     forming it again, which saves a matrix buffer (10 one-warp CTAs per SM) and two sparse
 //     products per layer;
 //   - a tube whose layers all hold the same blocks reads layer 0's H_ll and couplings for
-//     every layer (an L1-resident copy).
+//     every layer (an L1-resident copy);
+//   - the per-layer ring sums run in FP32 (a warp-wide FP64 operation costs the FP64 pipe of
+//     this part about as much as 60 FP32 ones); FP64 remains for the lead roots, eps - U and
+//     T(E), once per lane or layer.
 // Tile classes (CTA width): 1 warp for b <= 18 (6 x 5 tiles), 2 warps for b <= 27 (9 x 7), 4
-// warps for b <= 36 (12 x 9); wider blocks keep the shared-memory kernel.  Matrices are kept
+// warps for b <= 36 (12 x 9), at 10, 4 and 3 resident CTAs per SM; wider blocks keep the
+// shared-memory kernel.  Matrices are kept
 // with exact zero padding outside b x b, so padded rows and columns never feed a result.
 // Every output element, and every row, ring and T(E) sum, is evaluated in an order that does
 // not depend on the tile class, so all CTA widths give the same bits.
