@@ -297,6 +297,37 @@ class OraclePool:
                 p.kill()
 
 
+def mixed_against_stored_oracle():
+    """The mixed path with its defaults on the grid stored in tests/golden/mixed_cnt17_N1024.json
+    (the (17,0) N = 1024 workload's energies, its weights and Fermi factors, the stored contour
+    nodes) against the FP64 oracle's outputs stored there: norm-wise relative errors of n and T,
+    relative error of I.  The stored values were written by the oracle alone."""
+    path = os.path.join(ROOT, "tests", "golden", "mixed_cnt17_N1024.json")
+    if not os.path.exists(path):
+        return None
+    from paper_2407_14633_gb300 import negf, synth, workloads
+    with open(path) as fh:
+        gd = json.load(fh)
+    w = synth.mixed_precision(n_tube=gd["n_tube"], N=gd["N"], n_energies=gd["n_energies"])
+    E = np.asarray(w["E"], dtype=np.float64)
+    z = np.array([complex(*x) for x in gd["z"]])
+    c = np.array([complex(*x) for x in gd["c"]])
+    with negf.Context(precision=negf.PREC_MIXED) as ctx:
+        dev = ctx.device_create(gd["N"], block=gd["n_tube"], rings_per_block=1, n_chains=1)
+        ctx.build_cnt_realspace(dev, gd["n_tube"], gd["t"], gd["U_S"], gd["U_D"])
+        ctx.set_potential(dev, w["U"])
+        ctx.set_grid(dev, E, np.full(E.size, 2.0 / E.size), workloads._fermi(E - gd["mu_S"], gd["kT"]),
+                     workloads._fermi(E - gd["mu_D"], gd["kT"]), gd["eta"], z, c)
+        r = ctx.compute([dev])[0]
+    n_ref = np.array([float(x) for x in gd["n"]])
+    T_ref = np.array([float(x) for x in gd["T"]])
+    I_ref = float(gd["I"])
+    return {"n": float(np.max(np.abs(r["n"] - n_ref)) / np.max(np.abs(n_ref))),
+            "T": float(np.max(np.abs(r["T"] - T_ref)) / np.max(np.abs(T_ref))),
+            "I": abs(r["I"] - I_ref) / abs(I_ref),
+            "reference": "FP64 oracle values stored in tests/golden/mixed_cnt17_N1024.json, same grid"}
+
+
 def cpu_baseline_record(n_real=256, n_cont=16):
     """cpu_baseline: the oracle on every host core, with the one-core figure beside it (the
     same sample, one process)."""
@@ -542,6 +573,9 @@ def run_ours(args):
                                       "rel_err_vs_c128": {"n": mp["c64"]["rel_err_n"], "T": mp["c64"]["rel_err_T"],
                                                           "I": mp["c64"]["rel_err_I"]}},
                          "options": "flag_threshold 1e-3 (the default), edge_window 2 meV, growth criterion off"}
+        mo = mixed_against_stored_oracle()
+        if mo is not None:
+            line["mixed"]["rel_err_vs_oracle"] = mo
         sv = workloads.serving_sweep(n_requests=args.serving_requests)
         line["serving"] = {"workload": "iv_sweep_first%d_of_256_requests" % args.serving_requests,
                            "requests": sv["requests"], "converged": sv["converged_requests"], "tol": sv["tol"],
