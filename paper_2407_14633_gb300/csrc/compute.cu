@@ -26,7 +26,9 @@ int kernel_class(const Dev* d) { return d->block == 1 ? 0 : (d->block == 2 ? 1 :
 // 8-warp CTAs left 104 SMs with two CTAs and 48 with one; the eight-device mode-space case ran
 // 10% faster at two warps).  Groups of at least one item per SM are tuned over 1, 2, 4, 8 warps.
 constexpr int CHAIN_WARPS_DEFAULT = 2;
-size_t chain_smem(int warps) { return (size_t)warps * 32 * 33 * sizeof(double); }
+// shared memory of a thread-per-lane CTA: one 32 x 33 transpose buffer per warp, of the sweep's
+// element type
+size_t chain_smem(int warps, bool f32) { return (size_t)warps * 32 * 33 * (f32 ? sizeof(float) : sizeof(double)); }
 // tuning key of a thread-per-lane group: item counts are bucketed by powers of two, so a serving
 // loop whose batch changes step by step tunes once per bucket
 int chain_bucket(int n) {
@@ -355,7 +357,7 @@ static int tune_chain_width(Ctx* c, Plan& P, int g) {
   };
   std::vector<Cand> cand;
   for (int w : {1, 2, 4, 8}) {
-    const int occ = sweep_chain_occupancy_t(f32, cls, 32 * w, chain_smem(w));
+    const int occ = sweep_chain_occupancy_t(f32, cls, 32 * w, chain_smem(w, f32));
     const long long grid = std::min<long long>(std::min<long long>((long long)c->sms * occ, (n + w - 1) / w),
                                                max_warps / w);
     if (grid >= 1) cand.push_back({w, (int)grid});
@@ -632,11 +634,11 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
     const bool f32 = group_f32(g);
     int per_sm, wpb;
     if (cls < 2) {
-      per_sm = sweep_chain_occupancy_t(f32, cls, 32 * P.gw[g], chain_smem(P.gw[g]));
+      per_sm = sweep_chain_occupancy_t(f32, cls, 32 * P.gw[g], chain_smem(P.gw[g], f32));
       wpb = P.gw[g];
       if (tune_chain[g])   // staging for the most resident warps of any trial width
         for (int w : {1, 2, 4, 8}) {
-          const int occ = sweep_chain_occupancy_t(f32, cls, 32 * w, chain_smem(w));
+          const int occ = sweep_chain_occupancy_t(f32, cls, 32 * w, chain_smem(w, f32));
           const long long warps = std::min<long long>((long long)c->sms * occ * w, ((P.ncls[g] + w - 1) / w) * (long long)w);
           stage_bytes = std::max(stage_bytes, P.stride[g] * warps);
         }
@@ -670,7 +672,7 @@ int build_plan(Ctx* c, const std::vector<Dev*>& devs, const std::vector<ViewOver
         if (sm > 227 * 1024) return set_err(c, NEGF_EINVAL, "ring block too wide for shared memory");
         sweep_blk_occupancy_t(false, P.gw[g], P.gb[g], P.gm[g]);
       } else {
-        sweep_chain_occupancy_t(false, cls, 32 * P.gw[g + 5], chain_smem(P.gw[g + 5]));
+        sweep_chain_occupancy_t(false, cls, 32 * P.gw[g + 5], chain_smem(P.gw[g + 5], false));
       }
     }
 

@@ -449,25 +449,26 @@ __global__ void __launch_bounds__(256) sweep_b2_kernel(SweepArgs a) {
   }
 }
 
-static int launch_common(void (*kern)(SweepArgs), const SweepArgs& a, int grid, int block,
+static int launch_common(void (*kern)(SweepArgs), const SweepArgs& a, int grid, int block, size_t esize,
                          cudaStream_t s) {
-  // the dynamic shared memory limit was raised by sweep_chain_occupancy when planning
-  const size_t smem = (size_t)(block / 32) * 32 * 33 * sizeof(double);
+  // the dynamic shared memory limit was raised by sweep_chain_occupancy when planning; one
+  // 32 x 33 transpose buffer of the element type per warp
+  const size_t smem = (size_t)(block / 32) * 32 * 33 * esize;
   kern<<<grid, block, smem, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int launch_sweep_b1_f64(const SweepArgs& a, int grid, int block, cudaStream_t s) {
-  return launch_common(sweep_b1_kernel<double>, a, grid, block, s);
+  return launch_common(sweep_b1_kernel<double>, a, grid, block, sizeof(double), s);
 }
 int launch_sweep_b1_f32(const SweepArgs& a, int grid, int block, cudaStream_t s) {
-  return launch_common(sweep_b1_kernel<float>, a, grid, block, s);
+  return launch_common(sweep_b1_kernel<float>, a, grid, block, sizeof(float), s);
 }
 int launch_sweep_b2_f64(const SweepArgs& a, int grid, int block, cudaStream_t s) {
-  return launch_common(sweep_b2_kernel<double>, a, grid, block, s);
+  return launch_common(sweep_b2_kernel<double>, a, grid, block, sizeof(double), s);
 }
 int launch_sweep_b2_f32(const SweepArgs& a, int grid, int block, cudaStream_t s) {
-  return launch_common(sweep_b2_kernel<float>, a, grid, block, s);
+  return launch_common(sweep_b2_kernel<float>, a, grid, block, sizeof(float), s);
 }
 
 }  // namespace negf
